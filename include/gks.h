@@ -1,0 +1,172 @@
+/* gks.h -- C ABI of the GB300 gas-kinetic solver for 3D hybrid unstructured meshes.
+ *
+ * The library advances the semi-discrete finite-volume system dQ_i/dt = L(Q_i)
+ * (Yang, Pan & Xu, arXiv 2203.09047, Section 3.1, Eqs. semi and finite) on meshes of
+ * tetrahedra, pyramids, prisms and hexahedra, with the third-order WENO reconstruction of
+ * Section 2 (Eqs. weno and indicator), the time-dependent gas-kinetic flux of Section 3.2
+ * (Eqs. flux-1 and flux-2) integrated over each face by the 2x2 Gauss rule of Eq. flux-qud, and
+ * the two-stage fourth-order time discretisation of Section 3.3.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a gks_status; GKS_OK is 0. gks_last_error gives a text for the last
+ *    failure of a solver. Nothing is thrown across the ABI.
+ *  - Host arrays passed in are copied; the caller keeps ownership.
+ *  - State arrays are float64, structure of arrays [5][n_cells] (rho, rho U, rho V, rho W, rho E),
+ *    in the caller's cell order. Unless a call says otherwise they may be host or device
+ *    pointers (unified addressing decides); device pointers must be on the solver's device.
+ *    The library never frees or keeps caller pointers beyond a call.
+ *  - All device work is enqueued on the stream given to gks_init; calls that return values to
+ *    the host (gks_max_dt, status checks) synchronise that stream.
+ *  - A solver is not thread-safe. Results are bit-reproducible for a fixed mesh, parameters
+ *    and device: cell sums run in a fixed face order and no floating-point atomics are used.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GKS_OK = 0,
+  GKS_E_INVAL = 1,       /* bad argument */
+  GKS_E_NOMEM = 2,       /* device or host allocation failed */
+  GKS_E_CUDA = 3,        /* a CUDA runtime call failed */
+  GKS_E_MESH = 4,        /* non-conforming, inverted or unmatched cell/face */
+  GKS_E_SINGULAR = 5,    /* a stencil least-squares system is rank deficient */
+  GKS_E_NONPHYSICAL = 6, /* rho <= 0, p <= 0 or NaN in a state or a reconstructed value */
+  GKS_E_TIMEOUT = 7      /* reserved: a bounded device wait gave up */
+} gks_status;
+
+typedef struct gks_mesh gks_mesh;     /* opaque: topology, stencils, cell order */
+typedef struct gks_solver gks_solver; /* opaque: device geometry, buffers, state */
+
+/* Cell kinds: the value is the number of distinct vertices. */
+enum { GKS_TET = 4, GKS_PYR = 5, GKS_PRI = 6, GKS_HEX = 8 };
+/* Boundary condition per axis of the bounding box. */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_REFLECT = 1 };
+/* Flux variants (Section 3.2): the smooth flux of Eq. flux-2 read as
+ * g0 [1 - tau (a.u + A) + t A], or the full flux of Eq. flux-1. */
+enum { GKS_FLUX_SMOOTH = 0, GKS_FLUX_FULL = 1 };
+/* Collision time (Section 5): zero; inviscid tau = eps dt + C |pl-pr|/(pl+pr) dt;
+ * viscous tau = mu/p + C |pl-pr|/(pl+pr) dt with p the interface pressure. */
+enum { GKS_TAU_ZERO = 0, GKS_TAU_INVISCID = 1, GKS_TAU_VISCOUS = 2 };
+/* Arithmetic: FP64 everywhere, or FP32 reconstruction and flux with FP64 stencil
+ * differences, FP64 face sums and FP64 update. */
+enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
+
+typedef struct {
+  double gamma;      /* specific heat ratio; K = (5 - 3 gamma)/(gamma - 1) internal dofs */
+  double mu;         /* dynamic viscosity (0: Euler) */
+  double Pr;         /* Prandtl number: only 1 (the BGK value) is accepted */
+  int flux_mode;     /* GKS_FLUX_* */
+  int tau_model;     /* GKS_TAU_* */
+  double tau_eps;    /* eps of the inviscid collision time (Section 5: 0.01) */
+  double tau_C;      /* C of the pressure-jump term (Section 5: 1) */
+  double weno_gamma; /* linear weight of each sub-stencil (Section 2: 0.0125) */
+  double weno_eps;   /* epsilon of the nonlinear weights (not printed; default 1e-8) */
+  int weno_pow;      /* exponent of tau/(beta+eps) in the nonlinear weights (printed: 1) */
+  int precision;     /* GKS_PREC_* */
+} gks_params;
+
+/* Fill *p with the defaults above (gamma 1.4, Euler, smooth flux, zero collision time,
+ * weno_gamma 0.0125, weno_eps 1e-8, weno_pow 1, FP64). */
+void gks_params_default(gks_params* p);
+
+/* Build the mesh topology on the host.
+ *   xyz        [n_nodes][3] node coordinates.
+ *   cell_type  [n_cells] GKS_TET/PYR/PRI/HEX.
+ *   cell_nodes [n_cells][8] node indices in the degenerate-hexahedron slots of Section 2:
+ *              tet {p1 p2 p3 p3 p4 p4 p4 p4}, pyramid {p1 p2 p3 p4 p5 p5 p5 p5},
+ *              prism {p1 p2 p3 p3 p4 p5 p6 p6}, hex {p1..p8}; the face labels F_p of Section 2
+ *              (prism F3 read as {p1 p2 p5 p4}) fix the sub-stencils.
+ *   bc, lo, hi the bounding box [lo, hi] and a condition per axis. Faces on a periodic axis
+ *              match their translated image; unmatched faces must lie on a reflecting plane.
+ * Builds faces, the big stencils S_i (face neighbours, then neighbours of neighbours, as a set
+ * of (cell, periodic/mirror transform) pairs) and the sub-stencils of Section 2, and a
+ * Morton reorder of cells used internally. Errors: GKS_E_INVAL (bad type/index),
+ * GKS_E_MESH (face shared by more than two cells, unmatched face off a reflecting plane,
+ * periodic vertices not related by one translation), GKS_E_NOMEM. *out is NULL on error. */
+gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
+                           const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
+                           const double lo[3], const double hi[3], gks_mesh** out);
+
+/* Counts of a built mesh: cells, faces, total stencil entries. */
+gks_status gks_mesh_counts(const gks_mesh* m, int64_t* n_cells, int64_t* n_faces,
+                           int64_t* n_stencil);
+
+/* Last mesh-construction error text (valid until the next gks_mesh_create on this thread). */
+const char* gks_mesh_last_error(void);
+
+/* Create a solver on the current CUDA device: copies the mesh to the device, computes in FP64
+ * the cell and face quadrature (27-point trilinear, Section 2; 2x2 bilinear, Eq. flux-qud), the
+ * least-squares pseudo-inverses of every big stencil and sub-stencil, and stores them in the
+ * precision of p->precision. `stream` is a cudaStream_t (NULL: the legacy default stream) on
+ * which every later call enqueues its work. The mesh may be destroyed afterwards.
+ * Errors: GKS_E_INVAL (params), GKS_E_MESH (inverted cell), GKS_E_SINGULAR (rank-deficient
+ * stencil), GKS_E_NOMEM, GKS_E_CUDA. */
+gks_status gks_init(const gks_mesh* m, const gks_params* p, void* stream, gks_solver** out);
+
+/* Copy a state [5][n_cells] (caller order, host or device) into the solver. */
+gks_status gks_set_state(gks_solver* s, const double* Q);
+/* Copy the solver's state out to [5][n_cells] (caller order, host or device). */
+gks_status gks_get_state(gks_solver* s, double* Q);
+
+/* Largest stable step for the current state: cfl * min_i h_i / (|U_i| + c_i + 2 mu/(rho_i h_i)),
+ * h_i = |Omega_i| / (largest face area of cell i). Synchronises the stream.
+ * Errors: GKS_E_NONPHYSICAL. */
+gks_status gks_max_dt(gks_solver* s, double cfl, double* dt);
+
+/* Advance the solver's state by nsteps two-stage fourth-order steps of size dt (Section 3.3):
+ *   Q*      = Q^n + dt/2 L(Q^n) + dt^2/8 Lt(Q^n)
+ *   Q^{n+1} = Q^n + dt L(Q^n) + dt^2/6 (Lt(Q^n) + 2 Lt(Q*))
+ * where L and Lt = dL/dt come from the time-dependent face flux fitted on [0, dt/2] and [0, dt].
+ * Asynchronous on the solver's stream; a non-physical state is reported by gks_check. */
+gks_status gks_step(gks_solver* s, double dt, int nsteps);
+
+/* Synchronise the stream and report GKS_E_NONPHYSICAL if any earlier step or residual met
+ * rho <= 0, p <= 0 or NaN (the device flag is then cleared). */
+gks_status gks_check(gks_solver* s);
+
+/* Evaluate L(Q) and its time derivative Lt for a given state Q (Eq. finite):
+ *   L_i  = -(1/|Omega_i|) sum_f s_if F_f^n,   Lt_i = -(1/|Omega_i|) sum_f s_if dF_f/dt,
+ * F^n = (4 F(dt/2) - F(dt))/dt and dF/dt = 4 (F(dt) - 2 F(dt/2))/dt^2 from the time integrals
+ * F(delta) of the face flux. Q, L, Lt are [5][n_cells] in caller order, host or device.
+ * Does not change the solver's state. Synchronises the stream and returns GKS_E_NONPHYSICAL
+ * for a non-physical state or reconstructed value. */
+gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, double* Lt);
+
+/* Vector-Jacobian product of gks_residual at Q for a fixed dt:
+ *   gQ = (dL/dQ)^T gL + (dLt/dQ)^T gLt,
+ * all [5][n_cells] float64 in caller order, host or device. Reverse of the reconstruction,
+ * nonlinear weights and gas-kinetic flux; FP64 regardless of the solver's precision.
+ * Returns GKS_E_INVAL until the adjoint kernels are present in this build. */
+gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
+                            const double* gLt, double* gQ);
+
+/* Per-kernel timing for benchmarks and traces. With enable != 0 every later hot-path launch is
+ * bracketed by CUDA events on the solver's stream. gks_timing_read synchronises the stream and
+ * returns, for the kinds 0 reconstruction, 1 face flux, 2 face sum + update, the summed device
+ * milliseconds and the number of launches since the last read, then resets them. */
+gks_status gks_timing_enable(gks_solver* s, int enable);
+gks_status gks_timing_read(gks_solver* s, double ms[3], int64_t counts[3]);
+
+/* Algorithmic operation count of one face Gauss point of the flux kernel for a flux mode and
+ * collision-time model: *flops counts +, -, *, / (an FMA as two), *special counts exp, erfc and
+ * sqrt. Computed on the host by running the kernel's own templated arithmetic with a counting
+ * scalar type. Returns 0 on success. Not thread-safe. */
+int gks_flux_opcount(int flux_mode, int tau_model, double* flops, double* special);
+
+/* Text of the solver's last error. */
+const char* gks_last_error(const gks_solver* s);
+
+void gks_destroy(gks_solver* s);
+void gks_mesh_destroy(gks_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKS_H */

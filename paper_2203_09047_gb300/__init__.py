@@ -1,0 +1,272 @@
+"""GB300 gas-kinetic solver for 3D hybrid unstructured meshes (arXiv 2203.09047).
+
+A thin ctypes binding of the C ABI declared in include/gks.h. Every step of the hot path
+(reconstruction, gas-kinetic flux, face sums, two-stage update, time-step bound) runs in the CUDA
+kernels of libgks.so; this module only marshals arguments (torch tensors pass their data_ptr()).
+There is no CPU fallback: importing the binding without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded synthetic inputs)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgks.so")
+
+GKS_OK, GKS_E_INVAL, GKS_E_NOMEM, GKS_E_CUDA, GKS_E_MESH, GKS_E_SINGULAR, GKS_E_NONPHYSICAL, \
+    GKS_E_TIMEOUT = range(8)
+STATUS_NAMES = ["GKS_OK", "GKS_E_INVAL", "GKS_E_NOMEM", "GKS_E_CUDA", "GKS_E_MESH",
+                "GKS_E_SINGULAR", "GKS_E_NONPHYSICAL", "GKS_E_TIMEOUT"]
+GKS_FLUX_SMOOTH, GKS_FLUX_FULL = 0, 1
+GKS_TAU_ZERO, GKS_TAU_INVISCID, GKS_TAU_VISCOUS = 0, 1, 2
+GKS_PREC_FP64, GKS_PREC_MIXED = 0, 1
+
+
+class gks_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("flux_mode", ctypes.c_int), ("tau_model", ctypes.c_int),
+                ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double),
+                ("weno_gamma", ctypes.c_double), ("weno_eps", ctypes.c_double),
+                ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class GksError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgks.so (built by paper_2203_09047_gb300.build.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2203_09047_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, D, I64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+    st = ctypes.c_int
+    L.gks_params_default.argtypes = [ctypes.POINTER(gks_params)]
+    L.gks_params_default.restype = None
+    L.gks_mesh_create.argtypes = [I64, P, I64, P, P, P, P, P, ctypes.POINTER(P)]
+    L.gks_mesh_create.restype = st
+    L.gks_mesh_counts.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.gks_mesh_counts.restype = st
+    L.gks_mesh_last_error.argtypes = []
+    L.gks_mesh_last_error.restype = ctypes.c_char_p
+    L.gks_init.argtypes = [P, ctypes.POINTER(gks_params), P, ctypes.POINTER(P)]
+    L.gks_init.restype = st
+    L.gks_set_state.argtypes = [P, P]
+    L.gks_set_state.restype = st
+    L.gks_get_state.argtypes = [P, P]
+    L.gks_get_state.restype = st
+    L.gks_max_dt.argtypes = [P, ctypes.c_double, D]
+    L.gks_max_dt.restype = st
+    L.gks_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
+    L.gks_step.restype = st
+    L.gks_check.argtypes = [P]
+    L.gks_check.restype = st
+    L.gks_residual.argtypes = [P, P, ctypes.c_double, P, P]
+    L.gks_residual.restype = st
+    L.gks_residual_vjp.argtypes = [P, P, ctypes.c_double, P, P, P]
+    L.gks_residual_vjp.restype = st
+    L.gks_timing_enable.argtypes = [P, ctypes.c_int]
+    L.gks_timing_enable.restype = st
+    L.gks_timing_read.argtypes = [P, D, ctypes.POINTER(I64)]
+    L.gks_timing_read.restype = st
+    L.gks_flux_opcount.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
+    L.gks_flux_opcount.restype = ctypes.c_int
+    L.gks_last_error.argtypes = [P]
+    L.gks_last_error.restype = ctypes.c_char_p
+    L.gks_destroy.argtypes = [P]
+    L.gks_destroy.restype = None
+    L.gks_mesh_destroy.argtypes = [P]
+    L.gks_mesh_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _ptr(a) -> int:
+    """Raw address of a contiguous float64/int array: torch tensor (host or device) or numpy."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------------------- C-ABI names
+def gks_params_default(**overrides) -> gks_params:
+    p = gks_params()
+    load_library().gks_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def gks_mesh_create(xyz, cell_type, cell_nodes, bc, lo, hi) -> ctypes.c_void_p:
+    L = load_library()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    ct = np.ascontiguousarray(cell_type, dtype=np.int8)
+    cn = np.ascontiguousarray(cell_nodes, dtype=np.int64)
+    bc = np.ascontiguousarray(bc, dtype=np.int32)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    out = ctypes.c_void_p()
+    s = L.gks_mesh_create(len(xyz), xyz.ctypes.data, len(ct), ct.ctypes.data, cn.ctypes.data,
+                          bc.ctypes.data, lo.ctypes.data, hi.ctypes.data, ctypes.byref(out))
+    if s != GKS_OK:
+        raise GksError(s, L.gks_mesh_last_error().decode())
+    return out
+
+
+def gks_mesh_counts(mesh) -> tuple:
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().gks_mesh_counts(mesh, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def gks_init(mesh, params: gks_params, stream: int = 0) -> ctypes.c_void_p:
+    L = load_library()
+    out = ctypes.c_void_p()
+    s = L.gks_init(mesh, ctypes.byref(params), ctypes.c_void_p(stream), ctypes.byref(out))
+    if s != GKS_OK:
+        raise GksError(s, L.gks_mesh_last_error().decode())
+    return out
+
+
+def _check(s, solver=None):
+    if s != GKS_OK:
+        msg = load_library().gks_last_error(solver).decode() if solver else ""
+        raise GksError(s, msg)
+
+
+def gks_set_state(solver, Q):
+    _check(load_library().gks_set_state(solver, _ptr(Q)), solver)
+
+
+def gks_get_state(solver, Q):
+    _check(load_library().gks_get_state(solver, _ptr(Q)), solver)
+
+
+def gks_max_dt(solver, cfl: float) -> float:
+    out = ctypes.c_double()
+    _check(load_library().gks_max_dt(solver, cfl, ctypes.byref(out)), solver)
+    return out.value
+
+
+def gks_step(solver, dt: float, nsteps: int = 1):
+    _check(load_library().gks_step(solver, dt, nsteps), solver)
+
+
+def gks_check(solver):
+    _check(load_library().gks_check(solver), solver)
+
+
+def gks_residual(solver, Q, dt: float, L, Lt):
+    _check(load_library().gks_residual(solver, _ptr(Q), dt, _ptr(L), _ptr(Lt)), solver)
+
+
+def gks_residual_vjp(solver, Q, dt: float, gL, gLt, gQ):
+    _check(load_library().gks_residual_vjp(solver, _ptr(Q), dt, _ptr(gL), _ptr(gLt), _ptr(gQ)),
+           solver)
+
+
+def gks_timing_enable(solver, enable: bool = True):
+    _check(load_library().gks_timing_enable(solver, 1 if enable else 0), solver)
+
+
+def gks_timing_read(solver):
+    """(ms[3], counts[3]) for reconstruction, face flux, face sum + update since the last read."""
+    ms = (ctypes.c_double * 3)()
+    cnt = (ctypes.c_int64 * 3)()
+    _check(load_library().gks_timing_read(solver, ms, cnt), solver)
+    return list(ms), list(cnt)
+
+
+def gks_flux_opcount(flux_mode: int, tau_model: int):
+    """(flops, special-function calls) of one face Gauss point of the flux kernel."""
+    f, sp = ctypes.c_double(), ctypes.c_double()
+    if load_library().gks_flux_opcount(flux_mode, tau_model, ctypes.byref(f), ctypes.byref(sp)):
+        raise GksError(GKS_E_NONPHYSICAL, "op count failed")
+    return f.value, sp.value
+
+
+def gks_destroy(solver):
+    load_library().gks_destroy(solver)
+
+
+def gks_mesh_destroy(mesh):
+    load_library().gks_mesh_destroy(mesh)
+
+
+# ---------------------------------------------------------------------------- convenience
+class Solver:
+    """Owns a mesh handle and a solver handle; states are torch float64 tensors [5, n_cells]
+    on the solver's CUDA device (or pinned host tensors for host-side transfers)."""
+
+    def __init__(self, mesh: dict, stream=None, **params):
+        import torch
+        self.torch = torch
+        self.mesh_h = gks_mesh_create(mesh["xyz"], mesh["cell_type"], mesh["cell_nodes"],
+                                      mesh["bc"], mesh["lo"], mesh["hi"])
+        self.n_cells, self.n_faces, self.n_stencil = gks_mesh_counts(self.mesh_h)
+        self.params = gks_params_default(**params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        try:
+            self.h = gks_init(self.mesh_h, self.params, self.stream.cuda_stream)
+        finally:
+            gks_mesh_destroy(self.mesh_h)
+            self.mesh_h = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            gks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, Q):
+        t = self.torch
+        if isinstance(Q, np.ndarray):
+            Q = t.from_numpy(Q)
+        return Q.to(device="cuda", dtype=t.float64).contiguous()
+
+    def set_state(self, Q):
+        Q = self._dev(Q)
+        gks_set_state(self.h, Q)
+        self.stream.synchronize()
+
+    def get_state(self):
+        Q = self.torch.empty((5, self.n_cells), dtype=self.torch.float64, device="cuda")
+        gks_get_state(self.h, Q)
+        return Q
+
+    def max_dt(self, cfl: float) -> float:
+        return gks_max_dt(self.h, cfl)
+
+    def step(self, dt: float, nsteps: int = 1, check: bool = True):
+        gks_step(self.h, dt, nsteps)
+        if check:
+            gks_check(self.h)
+
+    def residual(self, Q, dt: float):
+        Q = self._dev(Q)
+        L = self.torch.empty_like(Q)
+        Lt = self.torch.empty_like(Q)
+        gks_residual(self.h, Q, dt, L, Lt)
+        return L, Lt

@@ -1,0 +1,486 @@
+// C ABI of the GB300 gas-kinetic solver: mesh and solver lifetime, state transfer, residual,
+// two-stage fourth-order stepping and the time-step bound.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gks_device.cuh"
+
+using namespace gks;
+
+namespace {
+thread_local std::string g_mesh_err;
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) return cudaSuccess;
+  return cudaMalloc((void**)p, sizeof(T) * (size_t)n);
+}
+template <class T>
+cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t st) {
+  cudaError_t e = dalloc(p, (int64_t)v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+}
+}  // namespace
+
+struct gks_solver {
+  gks_params prm;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  DevMesh m;
+  Geo64 g;
+  GeoR<double> gd;
+  GeoR<float> gf;
+  bool mixed = false;
+  // buffers (internal order)
+  double* Q = nullptr;      // state [5][nc]
+  double* Qs = nullptr;     // stage state
+  double* L = nullptr;      // [5][nc]
+  double* Lt = nullptr;
+  double* tmp = nullptr;    // staging in caller order [5][nc]
+  double* tmp2 = nullptr;   // second staging buffer
+  void* poly = nullptr;     // [50][nc] in R
+  void* fface = nullptr;    // [10][nf] in R
+  int* flag = nullptr;      // device status bits
+  int* bad_cell = nullptr;
+  double* dt_part = nullptr;
+  double* dt_out = nullptr;
+  double* h_dt = nullptr;   // pinned host scalar
+  std::vector<void*> owned;
+  std::string err;
+  // optional per-kernel event timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  // record a start event for kernel kind k; returns the index to close
+  int tick(int kind) {
+    if (!timing) return -1;
+    cudaEvent_t a = take_event(), b = take_event();
+    cudaEventRecord(a, st);
+    ev_used.push_back({kind, {a, b}});
+    return (int)ev_used.size() - 1;
+  }
+  void tock(int idx) {
+    if (idx >= 0) cudaEventRecord(ev_used[idx].second.second, st);
+  }
+
+  gks_status fail(gks_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  gks_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return GKS_E_CUDA;
+  }
+};
+
+namespace {
+
+template <class T>
+cudaError_t salloc(gks_solver* s, T** p, int64_t n) {
+  cudaError_t e = dalloc(p, n);
+  if (e == cudaSuccess && *p) s->owned.push_back((void*)*p);
+  return e;
+}
+template <class T>
+cudaError_t supload(gks_solver* s, T** p, const std::vector<T>& v) {
+  cudaError_t e = upload(p, v, s->st);
+  if (e == cudaSuccess && *p) s->owned.push_back((void*)*p);
+  return e;
+}
+
+template <class R>
+KParams<R> kparams(const gks_params& p) {
+  KParams<R> k;
+  k.gamma = (R)p.gamma;
+  k.K = (R)((5.0 - 3.0 * p.gamma) / (p.gamma - 1.0));
+  k.mu = (R)p.mu;
+  k.tau_eps = (R)p.tau_eps;
+  k.tau_C = (R)p.tau_C;
+  k.flux_mode = p.flux_mode;
+  k.tau_model = p.tau_model;
+  k.weno_gamma = (R)p.weno_gamma;
+  k.weno_eps = (R)p.weno_eps;
+  k.weno_pow = p.weno_pow;
+  return k;
+}
+
+template <class R>
+gks_status alloc_geo(gks_solver* s, GeoR<R>& g) {
+  const int64_t nc = s->m.nc, nf = s->m.nf;
+  cudaError_t e;
+  if ((e = salloc(s, &g.Ap, 9 * s->m.nst)) != cudaSuccess) return s->cuda_fail(e, "alloc A+");
+  if ((e = salloc(s, &g.Bp, 3 * s->m.nsb)) != cudaSuccess) return s->cuda_fail(e, "alloc B");
+  if ((e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc moments");
+  if ((e = salloc(s, &g.h, nc)) != cudaSuccess) return s->cuda_fail(e, "alloc h");
+  if ((e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face data");
+  R* poly = nullptr;
+  R* ff = nullptr;
+  if ((e = salloc(s, &poly, 50 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc poly");
+  if ((e = salloc(s, &ff, 10 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face flux");
+  s->poly = poly;
+  s->fface = ff;
+  return GKS_OK;
+}
+
+template <class R>
+void precompute_r(gks_solver* s, GeoR<R>& g) {
+  launch_geom_faces<R>(s->m, s->g, g, s->st);
+  launch_geom_hdt(s->m, s->g, s->st);
+  launch_geom_ls<R>(s->m, s->g, g, s->flag, s->bad_cell, s->st);
+  launch_cast_cells<R>(s->m, s->g, g, s->st);
+}
+
+// One residual evaluation on internal-order state Qin: recon -> flux -> gather(mode).
+template <class R>
+void residual_r(gks_solver* s, GeoR<R>& g, const double* Qin, double dt, int mode, double* L,
+                double* Lt, double* Qn, double* Qs) {
+  const KParams<R> kp = kparams<R>(s->prm);
+  int t = s->tick(0);
+  launch_recon<R>(s->m, g, kp, Qin, (R*)s->poly, s->st);
+  s->tock(t);
+  t = s->tick(1);
+  launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
+  s->tock(t);
+  t = s->tick(2);
+  launch_gather<R>(s->m, s->g, (const R*)s->fface, mode, dt, s->prm.gamma, L, Lt, Qn, Qs, s->flag,
+                   s->st);
+  s->tock(t);
+}
+
+void residual_any(gks_solver* s, const double* Qin, double dt, int mode, double* L, double* Lt,
+                  double* Qn, double* Qs) {
+  if (s->mixed)
+    residual_r<float>(s, s->gf, Qin, dt, mode, L, Lt, Qn, Qs);
+  else
+    residual_r<double>(s, s->gd, Qin, dt, mode, L, Lt, Qn, Qs);
+}
+
+gks_status read_flag(gks_solver* s, int* out) {
+  cudaError_t e = cudaMemcpyAsync(s->h_dt, s->flag, sizeof(int), cudaMemcpyDeviceToHost, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "status copy");
+  e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "stream synchronise");
+  std::memcpy(out, s->h_dt, sizeof(int));
+  return GKS_OK;
+}
+
+gks_status check_and_clear(gks_solver* s) {
+  int f = 0;
+  gks_status r = read_flag(s, &f);
+  if (r != GKS_OK) return r;
+  if (f) {
+    cudaMemsetAsync(s->flag, 0, sizeof(int), s->st);
+    if (f & kErrNonphysical)
+      return s->fail(GKS_E_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN)");
+    return s->fail(GKS_E_CUDA, "device status " + std::to_string(f));
+  }
+  return GKS_OK;
+}
+
+bool valid_params(const gks_params* p, std::string& why) {
+  if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) { why = "gamma must lie in (1, 5/3]"; return false; }
+  if (!(p->mu >= 0.0)) { why = "mu must be >= 0"; return false; }
+  if (p->Pr != 1.0) { why = "only Pr = 1 (the BGK value) is supported"; return false; }
+  if (p->flux_mode != GKS_FLUX_SMOOTH && p->flux_mode != GKS_FLUX_FULL) { why = "flux_mode"; return false; }
+  if (p->tau_model < GKS_TAU_ZERO || p->tau_model > GKS_TAU_VISCOUS) { why = "tau_model"; return false; }
+  if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
+  if (!(p->weno_eps > 0.0)) { why = "weno_eps must be > 0"; return false; }
+  if (p->weno_pow < 1 || p->weno_pow > 4) { why = "weno_pow must be 1..4"; return false; }
+  if (p->precision != GKS_PREC_FP64 && p->precision != GKS_PREC_MIXED) { why = "precision"; return false; }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gks_params_default(gks_params* p) {
+  if (!p) return;
+  p->gamma = 1.4;
+  p->mu = 0.0;
+  p->Pr = 1.0;
+  p->flux_mode = GKS_FLUX_SMOOTH;
+  p->tau_model = GKS_TAU_ZERO;
+  p->tau_eps = 0.01;
+  p->tau_C = 1.0;
+  p->weno_gamma = 0.0125;
+  p->weno_eps = 1e-8;
+  p->weno_pow = 1;
+  p->precision = GKS_PREC_FP64;
+}
+
+gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
+                           const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
+                           const double lo[3], const double hi[3], gks_mesh** out) {
+  if (!out) return GKS_E_INVAL;
+  *out = nullptr;
+  gks_mesh* m = new (std::nothrow) gks_mesh;
+  if (!m) return GKS_E_NOMEM;
+  gks_status st;
+  try {
+    st = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_nodes, bc, lo, hi, m->h, g_mesh_err);
+  } catch (const std::bad_alloc&) {
+    g_mesh_err = "host allocation failed";
+    st = GKS_E_NOMEM;
+  }
+  if (st != GKS_OK) {
+    delete m;
+    return st;
+  }
+  *out = m;
+  return GKS_OK;
+}
+
+gks_status gks_mesh_counts(const gks_mesh* m, int64_t* n_cells, int64_t* n_faces,
+                           int64_t* n_stencil) {
+  if (!m) return GKS_E_INVAL;
+  if (n_cells) *n_cells = m->h.n_cells;
+  if (n_faces) *n_faces = m->h.n_faces;
+  if (n_stencil) *n_stencil = (int64_t)m->h.st_idx.size();
+  return GKS_OK;
+}
+
+const char* gks_mesh_last_error(void) { return g_mesh_err.c_str(); }
+
+void gks_mesh_destroy(gks_mesh* m) { delete m; }
+
+gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks_solver** out) {
+  if (!out) return GKS_E_INVAL;
+  *out = nullptr;
+  if (!mesh || !p) return GKS_E_INVAL;
+  std::string why;
+  if (!valid_params(p, why)) {
+    g_mesh_err = why;
+    return GKS_E_INVAL;
+  }
+  gks_solver* s = new (std::nothrow) gks_solver;
+  if (!s) return GKS_E_NOMEM;
+  s->prm = *p;
+  s->st = (cudaStream_t)stream;
+  s->mixed = p->precision == GKS_PREC_MIXED;
+  cudaGetDevice(&s->device);
+  const HostMesh& h = mesh->h;
+  DevMesh& m = s->m;
+  m.nc = h.n_cells;
+  m.nf = h.n_faces;
+  m.nst = (int64_t)h.st_idx.size();
+  m.nsb = h.sb_ptr.back();
+  cudaError_t e = cudaSuccess;
+  auto bad = [&](const char* what) {
+    gks_status r = e == cudaErrorMemoryAllocation ? GKS_E_NOMEM : GKS_E_CUDA;
+    g_mesh_err = std::string(what) + ": " + cudaGetErrorString(e);
+    gks_destroy(s);
+    return r;
+  };
+  if ((e = supload(s, &m.perm, h.perm)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.type, h.type)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.cell_x, h.cell_x)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.f_owner, h.f_owner)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.f_nb, h.f_nb)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.f_wall, h.f_wall)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.f_vert, h.f_vert)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.f_shift, h.f_shift)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.cf_ptr, h.cf_ptr)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.cf_idx, h.cf_idx)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.st_ptr, h.st_ptr)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.st_idx, h.st_idx)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.st_xf, h.st_xf)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.st_sub, h.st_sub)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.n_sub, h.n_sub)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.sb_ptr, h.sb_ptr)) != cudaSuccess) return bad("upload");
+  const int64_t nc = m.nc, nf = m.nf;
+  if ((e = salloc(s, &s->g.vol, nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.cen, 3 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.h, nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.mom, 6 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.hdt, nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.farea, nf)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->Q, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->Qs, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->L, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->Lt, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->tmp, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->tmp2, 5 * nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->flag, 2)) != cudaSuccess) return bad("alloc");
+  s->bad_cell = s->flag + 1;
+  if ((e = salloc(s, &s->dt_part, dt_blocks(nc) + 1)) != cudaSuccess) return bad("alloc");
+  s->dt_out = s->dt_part + dt_blocks(nc);
+  if ((e = cudaMallocHost((void**)&s->h_dt, 16)) != cudaSuccess) return bad("alloc pinned");
+  const int init_flags[2] = {0, 0x7fffffff};
+  if ((e = cudaMemcpyAsync(s->flag, init_flags, sizeof(init_flags), cudaMemcpyHostToDevice, s->st)) !=
+      cudaSuccess)
+    return bad("memcpy");
+  gks_status r = s->mixed ? alloc_geo(s, s->gf) : alloc_geo(s, s->gd);
+  if (r != GKS_OK) {
+    g_mesh_err = s->err;
+    gks_destroy(s);
+    return r;
+  }
+  launch_geom_cells(s->m, s->g, s->flag, s->st);
+  if (s->mixed)
+    precompute_r(s, s->gf);
+  else
+    precompute_r(s, s->gd);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return bad("precompute launch");
+  int flags[2];
+  e = cudaMemcpyAsync(flags, s->flag, sizeof(flags), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return bad("precompute");
+  if (flags[0]) {
+    gks_status code = (flags[0] & kErrInverted) ? GKS_E_MESH : GKS_E_SINGULAR;
+    g_mesh_err = (flags[0] & kErrInverted) ? "inverted or degenerate cell"
+                                           : "rank-deficient stencil at internal cell " +
+                                                 std::to_string(flags[1]) + " (caller cell " +
+                                                 std::to_string(h.perm[flags[1] < nc ? flags[1] : 0]) + ")";
+    gks_destroy(s);
+    return code;
+  }
+  *out = s;
+  return GKS_OK;
+}
+
+gks_status gks_set_state(gks_solver* s, const double* Q) {
+  if (!s || !Q) return GKS_E_INVAL;
+  const int64_t nc = s->m.nc;
+  cudaError_t e = cudaMemcpyAsync(s->tmp, Q, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "set_state copy");
+  launch_permute_in(nc, s->m.perm, s->tmp, s->Q, s->st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "set_state");
+}
+
+gks_status gks_get_state(gks_solver* s, double* Q) {
+  if (!s || !Q) return GKS_E_INVAL;
+  const int64_t nc = s->m.nc;
+  launch_permute_out(nc, s->m.perm, s->Q, s->tmp, s->st);
+  cudaError_t e = cudaMemcpyAsync(Q, s->tmp, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "get_state copy");
+  e = cudaStreamSynchronize(s->st);
+  return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "get_state");
+}
+
+gks_status gks_max_dt(gks_solver* s, double cfl, double* dt) {
+  if (!s || !dt || !(cfl > 0)) return GKS_E_INVAL;
+  launch_check_state(s->m.nc, s->Q, s->prm.gamma, s->flag, s->st);
+  const int nb = dt_blocks(s->m.nc);
+  launch_dt(s->m.nc, s->Q, s->g.hdt, s->prm.gamma, s->prm.mu, s->dt_part, nb, s->dt_out, s->st);
+  gks_status r = check_and_clear(s);
+  if (r != GKS_OK) return r;
+  cudaError_t e = cudaMemcpyAsync(s->h_dt, s->dt_out, sizeof(double), cudaMemcpyDeviceToHost, s->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "max_dt");
+  *dt = cfl * s->h_dt[0];
+  return GKS_OK;
+}
+
+gks_status gks_step(gks_solver* s, double dt, int nsteps) {
+  if (!s || !(dt > 0) || nsteps < 0) return GKS_E_INVAL;
+  for (int k = 0; k < nsteps; ++k) {
+    // stage 1 on Q^n: L, Lt kept, Qs = Q* ; stage 2 on Q*: Q^{n+1} written into Q
+    residual_any(s, s->Q, dt, 1, s->L, s->Lt, s->Q, s->Qs);
+    residual_any(s, s->Qs, dt, 2, s->L, s->Lt, s->Q, s->Qs);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
+}
+
+gks_status gks_check(gks_solver* s) {
+  if (!s) return GKS_E_INVAL;
+  return check_and_clear(s);
+}
+
+gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, double* Lt) {
+  if (!s || !Q || !L || !Lt || !(dt > 0)) return GKS_E_INVAL;
+  const int64_t nc = s->m.nc;
+  cudaError_t e = cudaMemcpyAsync(s->tmp, Q, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "residual copy");
+  launch_permute_in(nc, s->m.perm, s->tmp, s->Qs, s->st);
+  launch_check_state(nc, s->Qs, s->prm.gamma, s->flag, s->st);
+  residual_any(s, s->Qs, dt, 0, s->tmp, s->tmp2, nullptr, nullptr);
+  // tmp, tmp2 hold L, Lt in internal order; write them out in caller order
+  launch_permute_out(nc, s->m.perm, s->tmp, s->Qs, s->st);
+  e = cudaMemcpyAsync(L, s->Qs, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "residual copy out");
+  launch_permute_out(nc, s->m.perm, s->tmp2, s->tmp, s->st);
+  e = cudaMemcpyAsync(Lt, s->tmp, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "residual copy out");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "residual launch");
+  return check_and_clear(s);
+}
+
+gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
+                            const double* gLt, double* gQ) {
+  if (!s) return GKS_E_INVAL;
+  (void)Q;
+  (void)dt;
+  (void)gL;
+  (void)gLt;
+  (void)gQ;
+  return s->fail(GKS_E_INVAL, "the residual VJP is not available in this build");
+}
+
+gks_status gks_timing_enable(gks_solver* s, int enable) {
+  if (!s) return GKS_E_INVAL;
+  s->timing = enable != 0;
+  return GKS_OK;
+}
+
+gks_status gks_timing_read(gks_solver* s, double ms[3], int64_t counts[3]) {
+  if (!s || !ms || !counts) return GKS_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(s->st);
+  if (e != cudaSuccess) return s->cuda_fail(e, "timing synchronise");
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = 0.0;
+    counts[k] = 0;
+  }
+  for (auto& u : s->ev_used) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess && u.first < 3) {
+      ms[u.first] += t;
+      counts[u.first] += 1;
+    }
+    s->ev_pool.push_back(u.second.first);
+    s->ev_pool.push_back(u.second.second);
+  }
+  s->ev_used.clear();
+  return GKS_OK;
+}
+
+const char* gks_last_error(const gks_solver* s) {
+  return s ? s->err.c_str() : g_mesh_err.c_str();
+}
+
+void gks_destroy(gks_solver* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  else cudaDeviceSynchronize();
+  for (void* p : s->owned) cudaFree(p);
+  for (auto& u : s->ev_used) {
+    cudaEventDestroy(u.second.first);
+    cudaEventDestroy(u.second.second);
+  }
+  for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  if (s->h_dt) cudaFreeHost(s->h_dt);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Device-side declarations shared by the CUDA translation units: the device copy of the mesh,
+// the precomputed geometry, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gks_internal.h"
+
+namespace gks {
+
+// Error bits of the device status word.
+enum : int {
+  kErrInverted = 1,     // a cell Jacobian <= 0 at a quadrature point
+  kErrSingular = 2,     // a least-squares system is rank deficient
+  kErrNonphysical = 4,  // rho <= 0, p <= 0 or NaN
+  kErrBigStencil = 8
+};
+
+// Mesh arrays on the device (internal order).
+struct DevMesh {
+  int64_t nc = 0, nf = 0, nst = 0, nsb = 0;
+  int32_t* perm = nullptr;
+  int8_t* type = nullptr;
+  double* cell_x = nullptr;   // [nc][24]
+  int32_t* f_owner = nullptr;
+  int32_t* f_nb = nullptr;
+  int8_t* f_wall = nullptr;
+  double* f_vert = nullptr;   // [nf][12]
+  double* f_shift = nullptr;  // [nf][3]
+  int32_t* cf_ptr = nullptr;
+  int32_t* cf_idx = nullptr;
+  int32_t* st_ptr = nullptr;
+  int32_t* st_idx = nullptr;
+  double* st_xf = nullptr;    // [nst][6]
+  uint8_t* st_sub = nullptr;
+  int8_t* n_sub = nullptr;
+  int32_t* sb_ptr = nullptr;
+};
+
+// FP64 geometry (always kept).
+struct Geo64 {
+  double* vol = nullptr;     // [nc]
+  double* cen = nullptr;     // [nc][3]
+  double* h = nullptr;       // [nc] |Omega|^(1/3)
+  double* mom = nullptr;     // [6][nc] second central moments / (|Omega| h^2): xx yy zz xy xz yz
+  double* hdt = nullptr;     // [nc] |Omega| / largest face area
+  double* farea = nullptr;   // [nf]
+};
+
+// Geometry in the arithmetic precision R of the hot path.
+template <class R>
+struct GeoR {
+  R* Ap = nullptr;   // per cell a block [9][K] (row n over the K stencil members)
+  R* Bp = nullptr;   // per (member, sub-stencil) pair: 3 coefficients, member-major order
+  R* mom = nullptr;  // [6][nc]
+  R* h = nullptr;    // [nc]
+  R* fgp = nullptr;  // [10][4 nf]: dl(3) dr(3) n1(3) w, index 4 f + gauss point
+};
+
+// Parameters of the hot kernels.
+template <class R>
+struct KParams {
+  R gamma, K, mu, tau_eps, tau_C;
+  int flux_mode, tau_model;
+  R weno_gamma, weno_eps;
+  int weno_pow;
+};
+
+// ---- precompute (gks_geom.cu) -------------------------------------------------------------
+void launch_geom_cells(const DevMesh& m, const Geo64& g, int* flag, cudaStream_t st);
+template <class R>
+void launch_geom_faces(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st);
+void launch_geom_hdt(const DevMesh& m, const Geo64& g, cudaStream_t st);
+template <class R>
+void launch_geom_ls(const DevMesh& m, const Geo64& g, GeoR<R>& gr, int* flag, int* bad_cell,
+                    cudaStream_t st);
+template <class R>
+void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st);
+
+// ---- hot path (gks_hot.cu) ----------------------------------------------------------------
+template <class R>
+void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const double* Q,
+                  R* poly, cudaStream_t st);
+template <class R>
+void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
+                 double dt, R* fface, int* flag, cudaStream_t st);
+// mode 0: write L, Lt. mode 1: stage 1 (store L, Lt; Qs = Qn + dt/2 L + dt^2/8 Lt).
+// mode 2: stage 2 (Qn += dt L0 + dt^2/6 (Lt0 + 2 Lt)).
+template <class R>
+void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
+                   double gamma, double* L, double* Lt, double* Qn, double* Qs, int* flag,
+                   cudaStream_t st);
+void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst,
+                       cudaStream_t st);
+void launch_permute_out(int64_t nc, const int32_t* perm, const double* src, double* dst,
+                        cudaStream_t st);
+void launch_check_state(int64_t nc, const double* Q, double gamma, int* flag, cudaStream_t st);
+void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, double mu,
+               double* partial, int nblocks, double* out, cudaStream_t st);
+int dt_blocks(int64_t nc);
+
+}  // namespace gks

@@ -1,0 +1,64 @@
+// Internal data structures shared by the host mesh builder, the device precompute and the
+// hot-path kernels of the GB300 gas-kinetic solver.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/gks.h"
+
+namespace gks {
+
+// Stencil entries carry the cell index in the low bits and a 3-bit mask of mirrored axes
+// (momentum components that change sign) in the top bits.
+constexpr int kFlipShift = 28;
+constexpr int32_t kCellMask = (1 << kFlipShift) - 1;
+constexpr int kMaxStencil = 64;  // largest big stencil accepted
+constexpr int kMaxSub = 8;       // largest number of sub-stencils (hexahedra, pyramids)
+
+// Affine per-axis map x' = s x + t between cell frames (periodic shift or mirror image).
+struct Xf {
+  int8_t s[3] = {1, 1, 1};
+  double t[3] = {0, 0, 0};
+};
+
+// Host-side mesh after topology, stencil and ordering work. Cells and faces are in the
+// internal (Morton) order; perm maps internal cell -> caller cell.
+struct HostMesh {
+  int64_t n_cells = 0, n_faces = 0;
+  int bc[3] = {0, 0, 0};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  std::vector<int32_t> perm;           // internal -> caller
+  std::vector<int8_t> type;            // internal order
+  std::vector<double> cell_x;          // [n][8][3] slot coordinates (internal order)
+  // faces
+  std::vector<int32_t> f_owner, f_nb;  // internal cell ids; nb = -1 on a reflecting wall
+  std::vector<int8_t> f_wall;          // wall axis or -1
+  std::vector<double> f_vert;          // [nf][4][3] oriented vertices in the owner frame
+  std::vector<double> f_shift;         // [nf][3] neighbour frame -> owner frame translation
+  // cell -> face incidence, fixed local-face order: (face << 1) | (1 if the cell is the nb side)
+  std::vector<int32_t> cf_ptr, cf_idx;
+  // big stencil (without the cell itself) and sub-stencil membership
+  std::vector<int32_t> st_ptr, st_idx;  // st_idx: cell | flip mask << kFlipShift
+  std::vector<double> st_xf;            // [n_st][6]: s[3], t[3] of the member transform
+  std::vector<uint8_t> st_sub;          // bit m set if the member is in sub-stencil m
+  std::vector<int8_t> n_sub;            // M per cell
+  std::vector<int32_t> sb_ptr;          // offset of each cell's (member, sub-stencil) pairs
+};
+
+struct DeviceGeom;  // defined in the CUDA sources
+
+}  // namespace gks
+
+struct gks_mesh {
+  gks::HostMesh h;
+};
+
+namespace gks {
+// Host mesh construction (gks_mesh.cpp). Returns a status and fills err.
+gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
+                           const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
+                           const double lo[3], const double hi[3], HostMesh& m,
+                           std::string& err);
+}  // namespace gks

@@ -1,0 +1,368 @@
+// Gas-kinetic flux at one Gauss point (Section 3.2), written for the GPU: closed-form
+// Maxwellian moments, closed-form slope solves, and the time-fitted flux F^n, dF/dt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gks {
+
+#define GKS_HD __host__ __device__ __forceinline__
+
+__device__ __forceinline__ double k_exp(double x) { return exp(x); }
+__device__ __forceinline__ float k_exp(float x) { return expf(x); }
+__device__ __forceinline__ double k_erfc(double x) { return erfc(x); }
+__device__ __forceinline__ float k_erfc(float x) { return erfcf(x); }
+__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float k_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double k_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float k_abs(float x) { return fabsf(x); }
+
+// Moments <u^k>, <v^l>, <w^m>, <xi^(2x)> of a unit-density Maxwellian (u possibly over a
+// half line).
+template <class R>
+struct Mom {
+  R u[7], v[6], w[6], xi[3];
+};
+
+// Full-line moments by the Gaussian recurrence <c^(n+1)> = C <c^n> + n/(2 lambda) <c^(n-1)>.
+template <class R, int N>
+GKS_HD void line_moments(R c, R half_inv_lam, R* out) {
+  out[0] = R(1);
+  out[1] = c;
+#pragma unroll
+  for (int n = 2; n < N; ++n) out[n] = c * out[n - 1] + R(n - 1) * half_inv_lam * out[n - 2];
+}
+
+// Moments of a Maxwellian with velocity (U,V,W) and lambda = rho/(2p). side = 0: full line in u,
+// +1: u > 0, -1: u < 0.
+template <class R>
+GKS_HD void maxwell_moments(R U, R V, R W, R lam, R K, int side, Mom<R>& M) {
+  const R hil = R(0.5) / lam;
+  line_moments<R, 6>(V, hil, M.v);
+  line_moments<R, 6>(W, hil, M.w);
+  if (side == 0) {
+    line_moments<R, 7>(U, hil, M.u);
+  } else {
+    const R sl = k_sqrt(lam);
+    const R s = R(side);
+    M.u[0] = R(0.5) * k_erfc(-s * sl * U);
+    M.u[1] = U * M.u[0] + s * R(0.28209479177387814) * k_exp(-lam * U * U) / sl;  // 1/(2 sqrt(pi))
+#pragma unroll
+    for (int n = 2; n < 7; ++n) M.u[n] = U * M.u[n - 1] + R(n - 1) * hil * M.u[n - 2];
+  }
+  M.xi[0] = R(1);
+  M.xi[1] = K * hil;
+  M.xi[2] = K * (K + R(2)) * hil * hil;
+}
+
+// <u^k v^l w^m xi^(2x) psi>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2).
+template <class R>
+GKS_HD void G(const Mom<R>& M, int k, int l, int m, int x, R o[5]) {
+  const R b = M.v[l] * M.w[m] * M.xi[x];
+  o[0] = M.u[k] * b;
+  o[1] = M.u[k + 1] * b;
+  o[2] = M.u[k] * M.v[l + 1] * M.w[m] * M.xi[x];
+  o[3] = M.u[k] * M.v[l] * M.w[m + 1] * M.xi[x];
+  o[4] = R(0.5) * (M.u[k + 2] * b + M.u[k] * M.v[l + 2] * M.w[m] * M.xi[x] +
+                   M.u[k] * M.v[l] * M.w[m + 2] * M.xi[x] + M.u[k] * M.v[l] * M.w[m] * M.xi[x + 1]);
+}
+
+// <a u^k v^l w^m psi> with a = a0 + a1 u + a2 v + a3 w + a4 (u^2+v^2+w^2+xi^2)/2.
+template <class R>
+GKS_HD void Ga(const Mom<R>& M, const R a[5], int k, int l, int m, R o[5]) {
+  R t[5];
+  G(M, k, l, m, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] = a[0] * t[q];
+  G(M, k + 1, l, m, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += a[1] * t[q];
+  G(M, k, l + 1, m, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += a[2] * t[q];
+  G(M, k, l, m + 1, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += a[3] * t[q];
+  const R h4 = R(0.5) * a[4];
+  G(M, k + 2, l, m, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
+  G(M, k, l + 2, m, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
+  G(M, k, l, m + 2, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
+  G(M, k, l, m, 1, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
+}
+
+// <u^k (a1 u + a2 v + a3 w) psi> for three slope polynomials a1, a2, a3.
+template <class R>
+GKS_HD void Gadotu(const Mom<R>& M, const R a[3][5], int k, R o[5]) {
+  R t[5];
+  Ga(M, a[0], k + 1, 0, 0, o);
+  Ga(M, a[1], k, 1, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += t[q];
+  Ga(M, a[2], k, 0, 1, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) o[q] += t[q];
+}
+
+// Solve <a psi> = b for the slope polynomial a of a Maxwellian (closed form of the 5x5 moment
+// system; b is the conserved-variable derivative divided by rho).
+template <class R>
+GKS_HD void slope_solve(R U, R V, R W, R lam, R K, const R b[5], R a[5]) {
+  const R q2 = U * U + V * V + W * W;
+  const R e2 = q2 + (K + R(3)) * R(0.5) / lam;
+  const R r1 = b[1] - U * b[0], r2 = b[2] - V * b[0], r3 = b[3] - W * b[0];
+  const R r4 = R(2) * b[4] - e2 * b[0];
+  a[4] = R(4) * lam * lam / (K + R(3)) * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
+  const R tl = R(2) * lam;
+  a[1] = tl * r1 - U * a[4];
+  a[2] = tl * r2 - V * a[4];
+  a[3] = tl * r3 - W * a[4];
+  a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * e2;
+}
+
+template <class R>
+struct Prim {
+  R rho, U, V, W, p, lam;
+};
+
+template <class R>
+GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
+  w.rho = q[0];
+  const R ir = R(1) / q[0];
+  w.U = q[1] * ir;
+  w.V = q[2] * ir;
+  w.W = q[3] * ir;
+  w.p = (gamma - R(1)) * (q[4] - R(0.5) * (q[1] * w.U + q[2] * w.V + q[3] * w.W));
+  w.lam = R(0.5) * w.rho / w.p;
+  return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
+}
+
+template <class R>
+struct FluxParams {
+  R gamma, K, mu, tau_eps, tau_C;
+  int full, tau_model;
+};
+
+// Time integrals over [0, d] of the six coefficients of Eq. flux-1.
+template <class R>
+GKS_HD void flux1_integrals(R tau, R d, R c[6]) {
+  const R e = k_exp(-d / tau);
+  const R om = R(1) - e;
+  c[0] = d - tau * om;
+  c[1] = R(2) * tau * tau * om - tau * d * (R(1) + e);
+  c[2] = R(0.5) * d * d - tau * d + tau * tau * om;
+  c[3] = tau * om;
+  c[4] = tau * d * e - R(2) * tau * tau * om;
+  c[5] = -tau * tau * om;
+}
+
+// Gauss-point flux in the local frame (u along the normal). ql/qr: conserved states;
+// dql/dqr[m]: their derivatives along n1, n2, n3 (momentum already in the local frame).
+// Writes Fn = F^n and Ft = dF/dt of the two-point time fit. Returns false for a non-physical
+// state.
+template <class R>
+GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
+                                            const R dql[3][5], const R qr[5], const R dqr[3][5],
+                                            R dt, R Fn[5], R Ft[5]) {
+  Prim<R> wl, wr, w0;
+  bool ok = to_prim(ql, P.gamma, wl) & to_prim(qr, P.gamma, wr);
+  if (!ok) return false;
+  Mom<R> Mlp, Mrn;
+  maxwell_moments(wl.U, wl.V, wl.W, wl.lam, P.K, +1, Mlp);
+  maxwell_moments(wr.U, wr.V, wr.W, wr.lam, P.K, -1, Mrn);
+  // interface equilibrium Q0 from the two half-space moments
+  R q0[5], t[5];
+  G(Mlp, 0, 0, 0, 0, q0);
+  G(Mrn, 0, 0, 0, 0, t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) q0[q] = wl.rho * q0[q] + wr.rho * t[q];
+  if (!to_prim(q0, P.gamma, w0)) return false;
+  Mom<R> M0;
+  maxwell_moments(w0.U, w0.V, w0.W, w0.lam, P.K, 0, M0);
+  // slopes of both sides in the three directions
+  R al[3][5], ar[3][5];
+  const R irl = R(1) / wl.rho, irr = R(1) / wr.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R b[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = dql[d][q] * irl;
+    slope_solve(wl.U, wl.V, wl.W, wl.lam, P.K, b, al[d]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = dqr[d][q] * irr;
+    slope_solve(wr.U, wr.V, wr.W, wr.lam, P.K, b, ar[d]);
+  }
+  // equilibrium slopes from the half-space moments, and the equilibrium time slope
+  R ab[3][5], Ab[5];
+  const R ir0 = R(1) / w0.rho;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R sl[5], sr[5], b[5];
+    Ga(Mlp, al[d], 0, 0, 0, sl);
+    Ga(Mrn, ar[d], 0, 0, 0, sr);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = (wl.rho * sl[q] + wr.rho * sr[q]) * ir0;
+    slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, ab[d]);
+  }
+  {
+    R b[5];
+    Gadotu(M0, ab, 0, b);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = -b[q];
+    slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, Ab);
+  }
+  R tau = R(0);
+  const R dp = k_abs((wl.p - wr.p) / (wl.p + wr.p));
+  if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
+  if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
+  // equilibrium flux moments
+  R e0[5], e1[5], e2[5];
+  G(M0, 1, 0, 0, 0, e0);
+  Gadotu(M0, ab, 1, e1);
+  Ga(M0, Ab, 1, 0, 0, e2);
+  if (!P.full) {
+    // F(delta) = rho0 [delta e0 - tau delta (e1 + e2) + delta^2/2 e2]: the fit is exact.
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      Fn[q] = w0.rho * (e0[q] - tau * (e1[q] + e2[q]));
+      Ft[q] = w0.rho * e2[q];
+    }
+    return true;
+  }
+  // full flux: non-equilibrium parts need the time slopes of both sides
+  Mom<R> Ml, Mr;
+  maxwell_moments(wl.U, wl.V, wl.W, wl.lam, P.K, 0, Ml);
+  maxwell_moments(wr.U, wr.V, wr.W, wr.lam, P.K, 0, Mr);
+  R Al[5], Ar[5];
+  {
+    R b[5];
+    Gadotu(Ml, al, 0, b);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = -b[q];
+    slope_solve(wl.U, wl.V, wl.W, wl.lam, P.K, b, Al);
+    Gadotu(Mr, ar, 0, b);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b[q] = -b[q];
+    slope_solve(wr.U, wr.V, wr.W, wr.lam, P.K, b, Ar);
+  }
+  R cn[6], ct[6];
+  if (tau > R(0)) {
+    R ch[6], cf[6];
+    flux1_integrals(tau, R(0.5) * dt, ch);
+    flux1_integrals(tau, dt, cf);
+    const R idt = R(1) / dt;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      cn[q] = (R(4) * ch[q] - cf[q]) * idt;
+      ct[q] = R(4) * (cf[q] - R(2) * ch[q]) * idt * idt;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) cn[q] = ct[q] = R(0);
+    cn[0] = R(1);
+    ct[2] = R(1);
+  }
+  R nl0[5], nl1[5], nl2[5], nr0[5], nr1[5], nr2[5];
+  G(Mlp, 1, 0, 0, 0, nl0);
+  Gadotu(Mlp, al, 1, nl1);
+  Ga(Mlp, Al, 1, 0, 0, nl2);
+  G(Mrn, 1, 0, 0, 0, nr0);
+  Gadotu(Mrn, ar, 1, nr1);
+  Ga(Mrn, Ar, 1, 0, 0, nr2);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const R geq_n = cn[0] * e0[q] + cn[1] * e1[q] + cn[2] * e2[q];
+    const R geq_t = ct[0] * e0[q] + ct[1] * e1[q] + ct[2] * e2[q];
+    const R gl_n = cn[3] * nl0[q] + cn[4] * nl1[q] + cn[5] * nl2[q];
+    const R gl_t = ct[3] * nl0[q] + ct[4] * nl1[q] + ct[5] * nl2[q];
+    const R gr_n = cn[3] * nr0[q] + cn[4] * nr1[q] + cn[5] * nr2[q];
+    const R gr_t = ct[3] * nr0[q] + ct[4] * nr1[q] + ct[5] * nr2[q];
+    Fn[q] = w0.rho * geq_n + wl.rho * gl_n + wr.rho * gr_n;
+    Ft[q] = w0.rho * geq_t + wl.rho * gl_t + wr.rho * gr_t;
+  }
+  return true;
+}
+
+// Value and gradient at offset d of a cell polynomial c[v][j] in physical offsets from the
+// centroid: Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz
+// + c9 dydz. `coef(v, j)` returns coefficient j of variable v.
+template <class R, class Coef>
+GKS_HD void eval_poly(const Coef& coef, const R d[3], R val[5], R grad[5][3]) {
+  const R xx = d[0] * d[0], yy = d[1] * d[1], zz = d[2] * d[2];
+  const R xy = d[0] * d[1], xz = d[0] * d[2], yz = d[1] * d[2];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    R k[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) k[j] = coef(v, j);
+    val[v] = k[0] + k[1] * d[0] + k[2] * d[1] + k[3] * d[2] + k[4] * xx + k[5] * yy + k[6] * zz +
+             k[7] * xy + k[8] * xz + k[9] * yz;
+    grad[v][0] = k[1] + R(2) * k[4] * d[0] + k[7] * d[1] + k[8] * d[2];
+    grad[v][1] = k[2] + R(2) * k[5] * d[1] + k[7] * d[0] + k[9] * d[2];
+    grad[v][2] = k[3] + R(2) * k[6] * d[2] + k[8] * d[0] + k[9] * d[1];
+  }
+}
+
+// Whole Gauss-point contribution in the global frame. Left/right values and gradients are
+// rotated into the local frame (n1 the unit normal, n2 = n1 x e_k / |n1 x e_k| with e_k the axis
+// least aligned with n1, n3 = n1 x n2), the local flux is computed, rotated back and multiplied
+// by the quadrature weight w: acc[0..4] = w F^n, acc[5..9] = w dF/dt.
+template <class R>
+GKS_HD bool gp_flux_global(const FluxParams<R>& P, const R vl[5], const R gl[5][3], const R vr[5],
+                           const R gr[5][3], const R n1[3], R w, R dt, R acc[10]) {
+  int kk = 0;
+  if (k_abs(n1[1]) < k_abs(n1[kk])) kk = 1;
+  if (k_abs(n1[2]) < k_abs(n1[kk])) kk = 2;
+  R n2[3];
+  if (kk == 0) { n2[0] = R(0); n2[1] = n1[2]; n2[2] = -n1[1]; }
+  else if (kk == 1) { n2[0] = -n1[2]; n2[1] = R(0); n2[2] = n1[0]; }
+  else { n2[0] = n1[1]; n2[1] = -n1[0]; n2[2] = R(0); }
+  const R il = R(1) / k_sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
+  n2[0] = n2[0] * il; n2[1] = n2[1] * il; n2[2] = n2[2] * il;
+  const R n3[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2],
+                   n1[0] * n2[1] - n1[1] * n2[0]};
+  const R* nm[3] = {n1, n2, n3};
+  R ql[5], qr[5], dql[3][5], dqr[3][5];
+  ql[0] = vl[0]; ql[4] = vl[4]; qr[0] = vr[0]; qr[4] = vr[4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    ql[1 + d] = vl[1] * nm[d][0] + vl[2] * nm[d][1] + vl[3] * nm[d][2];
+    qr[1 + d] = vr[1] * nm[d][0] + vr[2] * nm[d][1] + vr[3] * nm[d][2];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R sl[5], sr[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sl[v] = gl[v][0] * nm[d][0] + gl[v][1] * nm[d][1] + gl[v][2] * nm[d][2];
+      sr[v] = gr[v][0] * nm[d][0] + gr[v][1] * nm[d][1] + gr[v][2] * nm[d][2];
+    }
+    dql[d][0] = sl[0]; dql[d][4] = sl[4]; dqr[d][0] = sr[0]; dqr[d][4] = sr[4];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      dql[d][1 + e] = sl[1] * nm[e][0] + sl[2] * nm[e][1] + sl[3] * nm[e][2];
+      dqr[d][1 + e] = sr[1] * nm[e][0] + sr[2] * nm[e][1] + sr[3] * nm[e][2];
+    }
+  }
+  R Fn[5], Ft[5];
+  if (!gks_gp_flux(P, ql, dql, qr, dqr, dt, Fn, Ft)) return false;
+  acc[0] = w * Fn[0];
+  acc[4] = w * Fn[4];
+  acc[5] = w * Ft[0];
+  acc[9] = w * Ft[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc[1 + a] = w * (Fn[1] * n1[a] + Fn[2] * n2[a] + Fn[3] * n3[a]);
+    acc[6 + a] = w * (Ft[1] * n1[a] + Ft[2] * n2[a] + Ft[3] * n3[a]);
+  }
+  return true;
+}
+
+}  // namespace gks

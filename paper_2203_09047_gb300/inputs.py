@@ -144,59 +144,68 @@ def layered_box_mesh(n: int, layers="hybrid8", lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0,
         u = uniform01(seed, (3 * ids[:, None] + np.arange(3, dtype=np.uint64)[None, :]).ravel())
         xyz[ids] += ((2.0 * u - 1.0) * jitter).reshape(-1, 3) * h[None, :]
 
-    types, nodes = [], []
+    # vectorised over the n x n cubes of each layer (x fastest, then y)
+    jj2, ii2 = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    ii2, jj2 = ii2.ravel(), jj2.ravel()
     kuhn = _kuhn_paths()
+    blocks_t, blocks_n = [], []
 
-    def add(t, slots):
-        types.append(t)
-        nodes.append(slots)
+    def emit(t, slots_list):
+        """slots_list: list over the cells of one cube of [8] node-id arrays (one per cube);
+        cells are interleaved cube by cube."""
+        arr = np.stack([np.stack(sl, axis=1) for sl in slots_list], axis=1)  # [cubes, cells, 8]
+        blocks_n.append(arr.reshape(-1, 8))
+        blocks_t.append(np.broadcast_to(np.asarray(t, dtype=np.int8)[None, :], arr.shape[:2]).reshape(-1))
 
-    def add_tet(a, b, c, d):
-        if _signed_vol(xyz, a, b, c, d) < 0.0:
-            b, c = c, b
-        add(TET, [a, b, c, c, d, d, d, d])
+    def oriented_tet(a, b, c, d):
+        vol = np.einsum("ij,ij->i", np.cross(xyz[b] - xyz[a], xyz[c] - xyz[a]), xyz[d] - xyz[a])
+        flip = vol < 0.0
+        b2 = np.where(flip, c, b)
+        c2 = np.where(flip, b, c)
+        return [a, b2, c2, c2, d, d, d, d]
 
     for k, kind in enumerate(layers):
-        for j in range(n):
-            for i in range(n):
-                def V(a, b, c):
-                    return lid(i + a, j + b, k + c)
-                if kind == "hex":
-                    add(HEX, [V(0, 0, 0), V(1, 0, 0), V(1, 1, 0), V(0, 1, 0),
-                              V(0, 0, 1), V(1, 0, 1), V(1, 1, 1), V(0, 1, 1)])
-                elif kind == "prism":
-                    # triangles in the yz planes x = x0 (p1 p2 p3) and x = x1 (p4 p5 p6)
-                    for tri in (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1))):
-                        b0 = [V(0, y, z) for (y, z) in tri]
-                        t0 = [V(1, y, z) for (y, z) in tri]
-                        add(PRI, [b0[0], b0[1], b0[2], b0[2], t0[0], t0[1], t0[2], t0[2]])
-                elif kind in ("trans", "transm"):
-                    c = centre[(i, j, k)]
-                    bottom = [V(0, 0, 0), V(1, 0, 0), V(1, 1, 0), V(0, 1, 0)]
-                    top = [V(0, 0, 1), V(0, 1, 1), V(1, 1, 1), V(1, 0, 1)]
-                    sides = [[V(0, 0, 0), V(0, 1, 0), V(0, 1, 1), V(0, 0, 1)],   # x = x0
-                             [V(1, 0, 0), V(1, 0, 1), V(1, 1, 1), V(1, 1, 0)],   # x = x1
-                             [V(0, 0, 0), V(0, 0, 1), V(1, 0, 1), V(1, 0, 0)],   # y = y0
-                             [V(0, 1, 0), V(1, 1, 0), V(1, 1, 1), V(0, 1, 1)]]   # y = y1
-                    quads = list(sides)
-                    if kind == "trans":
-                        quads.insert(0, bottom)
-                        split_z = 1
-                    else:
-                        quads.append(top)
-                        split_z = 0
-                    for q in quads:
-                        add(PYR, [q[0], q[1], q[2], q[3], c, c, c, c])
-                    a0, a1 = V(0, 0, split_z), V(1, 1, split_z)
-                    add_tet(a0, V(1, 0, split_z), a1, c)
-                    add_tet(a0, a1, V(0, 1, split_z), c)
-                elif kind == "tet":
-                    for path in kuhn:
-                        add_tet(*[V(*p) for p in path])
-                else:
-                    raise ValueError(kind)
-    cell_type = np.array(types, dtype=np.int8)
-    cell_nodes = np.array(nodes, dtype=np.int64)
+        def V(a, b, c):
+            return lid(ii2 + a, jj2 + b, k + c)
+        if kind == "hex":
+            emit([HEX], [[V(0, 0, 0), V(1, 0, 0), V(1, 1, 0), V(0, 1, 0),
+                          V(0, 0, 1), V(1, 0, 1), V(1, 1, 1), V(0, 1, 1)]])
+        elif kind == "prism":
+            # triangles in the yz planes x = x0 (p1 p2 p3) and x = x1 (p4 p5 p6)
+            cells = []
+            for tri in (((0, 0), (1, 0), (1, 1)), ((0, 0), (1, 1), (0, 1))):
+                b0 = [V(0, y, z) for (y, z) in tri]
+                t0 = [V(1, y, z) for (y, z) in tri]
+                cells.append([b0[0], b0[1], b0[2], b0[2], t0[0], t0[1], t0[2], t0[2]])
+            emit([PRI, PRI], cells)
+        elif kind in ("trans", "transm"):
+            c = np.array([centre[(i, j, k)] for j, i in zip(jj2, ii2)], dtype=np.int64)
+            bottom = [V(0, 0, 0), V(1, 0, 0), V(1, 1, 0), V(0, 1, 0)]
+            top = [V(0, 0, 1), V(0, 1, 1), V(1, 1, 1), V(1, 0, 1)]
+            sides = [[V(0, 0, 0), V(0, 1, 0), V(0, 1, 1), V(0, 0, 1)],   # x = x0
+                     [V(1, 0, 0), V(1, 0, 1), V(1, 1, 1), V(1, 1, 0)],   # x = x1
+                     [V(0, 0, 0), V(0, 0, 1), V(1, 0, 1), V(1, 0, 0)],   # y = y0
+                     [V(0, 1, 0), V(1, 1, 0), V(1, 1, 1), V(0, 1, 1)]]   # y = y1
+            quads = list(sides)
+            if kind == "trans":
+                quads.insert(0, bottom)
+                split_z = 1
+            else:
+                quads.append(top)
+                split_z = 0
+            cells = [[q[0], q[1], q[2], q[3], c, c, c, c] for q in quads]
+            a0, a1 = V(0, 0, split_z), V(1, 1, split_z)
+            cells.append(oriented_tet(a0, V(1, 0, split_z), a1, c))
+            cells.append(oriented_tet(a0, a1, V(0, 1, split_z), c))
+            emit([PYR] * 5 + [TET, TET], cells)
+        elif kind == "tet":
+            emit([TET] * 6, [oriented_tet(*[V(*p) for p in path]) for path in kuhn])
+        else:
+            raise ValueError(kind)
+    types = np.concatenate(blocks_t)
+    nodes = np.concatenate(blocks_n)
+    cell_type = np.ascontiguousarray(types, dtype=np.int8)
+    cell_nodes = np.ascontiguousarray(nodes, dtype=np.int64)
     return {"xyz": np.ascontiguousarray(xyz), "cell_type": cell_type, "cell_nodes": cell_nodes,
             "bc": tuple(int(b) for b in bc), "lo": tuple(float(v) for v in lo),
             "hi": tuple(float(v) for v in hi), "n": n, "layers": tuple(layers)}
