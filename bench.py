@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Throughput of the two-stage fourth-order gas-kinetic step on a 3D hybrid unstructured mesh.
+
+Workload: the smooth advection case (density sine wave, U = V = W = 1, p = 1, gamma = 1.4) on the
+layered hybrid box mesh with 64 cubes per direction (1,048,576 cells: hexahedra, prisms, pyramids
+and tetrahedra, interior nodes jittered +-0.1 h, seed 1), periodic [0,2]^3, Euler with the smooth
+flux and zero collision time, CFL 0.5. A step is one S2O4 step (two stages of reconstruction,
+face flux and face sums + update) over the whole mesh; the metric counts cell-stage updates/s.
+
+The headline value is the mixed-precision path (FP32 reconstruction and flux, FP64 sums and
+update); the FP64 path is measured beside it. Inputs (geometry ~1 GB) are larger than L2.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-stage updates/s, FP32-bulk vs FP64, % roofline at stated error"
+UNIT = "cell-stage/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
+SM_MAX_GHZ = 2.07
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="cubes per direction")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 path (default: steps // 4, at least 3)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock and throttle-reason samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.rows = []
+        self.proc = None
+        self.device = device
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def workload_desc(n, nc=None, nf=None):
+    # the hybrid 8-layer pattern has 4 cells and 9.125 faces per cube
+    nc = nc if nc is not None else 4 * n ** 3
+    nf = nf if nf is not None else 73 * n ** 3 // 8
+    return {"workload": f"advection, hybrid layered box {n}^3 cubes ({nc} cells, {nf} faces), "
+                        "periodic [0,2]^3, jitter 0.1h seed 1, Euler smooth flux tau=0, CFL 0.5",
+            "cells": nc, "faces": nf, "cubes_per_dir": n, "flux": "smooth (Eq. flux-2)",
+            "tau": "zero", "cfl": 0.5, "gamma": 1.4,
+            "l2": "inputs larger than L2 (geometry and state > 1 GB); no flush"}
+
+
+# ------------------------------------------------------------------------------ oracle timing
+def time_oracle(n_sample: int, min_seconds: float, max_steps: int | None = None):
+    """Steps of the FP64 CPU oracle on the same generator at n_sample cubes per direction."""
+    import oracle
+    from paper_2203_09047_gb300 import inputs as I
+    m = I.layered_box_mesh(n_sample, "hybrid8")
+    om = oracle.Mesh(m)
+    P = oracle.params_vec()
+    Q = I.advection_state(m)
+    dt = om.max_dt(P, Q, 0.5)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        Q = om.step(P, Q, dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= min_seconds):
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return om.n_cells, steps, el, cores
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    # each step a bounded sample: the 8^3-cube mesh of the same generator (2048 cells)
+    n_sample = 8
+    from paper_2203_09047_gb300 import inputs as I
+    m = I.layered_box_mesh(n_sample, "hybrid8")
+    om = oracle.Mesh(m)
+    P = oracle.params_vec()
+    Q = I.advection_state(m)
+    dt = om.max_dt(P, Q, 0.5)
+    for _ in range(args.warmup):
+        Q = om.step(P, Q, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q = om.step(P, Q, dt, 1)
+    el = time.perf_counter() - t0
+    nc = om.n_cells
+    value = nc * 2 * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"{nc}-cell hybrid box (8^3 cubes, same generator) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(args.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    import paper_2203_09047_gb300 as gks
+    from paper_2203_09047_gb300 import build, inputs as I
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    gks.load_library()
+
+    mesh_dict = I.layered_box_mesh(args.n, "hybrid8")
+    Q0 = I.advection_state(mesh_dict)
+    mesh = gks.Mesh(mesh_dict)
+    stream = torch.cuda.Stream()
+    results = {}
+
+    def measure(precision, steps, warmup, timed_kernels=True):
+        S = gks.Solver(mesh, stream=stream, precision=precision)
+        S.set_state(Q0)
+        dt = S.max_dt(0.5)
+        for _ in range(warmup):
+            S.step(dt, 1, check=False)
+        gks.gks_check(S.h)
+        gks.gks_timing_read(S.h)  # reset
+        if timed_kernels:
+            gks.gks_timing_enable(S.h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            gks.gks_step(S.h, dt, steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        kms, kcnt = gks.gks_timing_read(S.h)
+        gks.gks_timing_enable(S.h, False)
+        gks.gks_check(S.h)
+        return dict(solver=S, dt=dt, ms=ms, kms=kms, kcnt=kcnt, clocks=clk.summary())
+
+    mixed = measure(gks.GKS_PREC_MIXED, args.steps, args.warmup)
+    S = mixed["solver"]
+    nc, nf = S.n_cells, S.n_faces
+    ms_total = mixed["ms"]
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * nc * 2 * args.steps / (ms_total * 1e-3)
+
+    # FP64 path on the same inputs and dt
+    fp64_steps = args.fp64_steps or max(3, args.steps // 4)
+    fp64 = measure(gks.GKS_PREC_FP64, fp64_steps, 2)
+    v64 = nc * 2 * fp64_steps / (fp64["ms"] * 1e-3)
+
+    # error of the mixed path against the FP64 path after the same steps from the same state
+    def advance(precision, k):
+        T = gks.Solver(mesh, stream=stream, precision=precision)
+        T.set_state(Q0)
+        T.step(mixed["dt"], k)
+        out = T.get_state().double().cpu().numpy()
+        T.close()
+        return out
+    k_err = 10
+    qm, qd = advance(gks.GKS_PREC_MIXED, k_err), advance(gks.GKS_PREC_FP64, k_err)
+    err = float(np.linalg.norm(qm - qd) / np.linalg.norm(qd))
+
+    # rooflines
+    bytes_k = gks.gks_kernel_bytes(S.h)
+    hbm, hbm_src = peaks()
+    flops_gp, special_gp = gks.gks_flux_opcount(0, 0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ * 1e-3  # TFLOP/s
+    fp64_peak = SM_COUNT * FP64_LANES_PER_SM * 2 * SM_MAX_GHZ * 1e-3
+
+    def kernel_table(res, is_mixed):
+        names = ["recon", "flux", "gather"]
+        out = {}
+        tot = sum(res["kms"])
+        for k in range(3):
+            n = max(res["kcnt"][k], 1)
+            avg_ms = res["kms"][k] / n
+            d = {"launches": res["kcnt"][k], "avg_ms": avg_ms, "share": res["kms"][k] / tot if tot else None,
+                 "gbs": bytes_k[k] * (1 if is_mixed else 1) / (avg_ms * 1e-3) / 1e9 if avg_ms else None}
+            out[names[k]] = d
+        fl = flops_gp * 4 * nf
+        out["flux"]["tflops"] = fl / (out["flux"]["avg_ms"] * 1e-3) / 1e12
+        return out
+
+    kt = kernel_table(mixed, True)
+    # bytes of the FP64 solver differ (8-byte geometry): ask that solver
+    bytes64 = gks.gks_kernel_bytes(fp64["solver"].h)
+    kt64 = kernel_table(fp64, False)
+    for k, name in enumerate(["recon", "flux", "gather"]):
+        kt64[name]["gbs"] = bytes64[k] / (kt64[name]["avg_ms"] * 1e-3) / 1e9
+
+    def roof_for(table, is_mixed):
+        dom = max(table, key=lambda k: table[k]["share"] or 0)
+        if dom == "flux":
+            peak = fp32_peak if is_mixed else fp64_peak
+            ach = table["flux"]["tflops"]
+            return {"kernel": f"k_flux<{'float' if is_mixed else 'double'}>", "bound": "alu",
+                    "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "traffic": None,
+                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM if is_mixed else FP64_LANES_PER_SM}"
+                                   f" {'FP32' if is_mixed else 'FP64'} FMA lanes x 2 x {SM_MAX_GHZ} GHz",
+                    "flops_per_gauss_point": flops_gp, "special_per_gauss_point": special_gp}
+        ach = table[dom]["gbs"]
+        return {"kernel": f"k_{dom}", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_desc(args.n, nc, nf),
+        "clocks": mixed["clocks"],
+        "gpu_launches": int(sum(mixed["kcnt"])),
+        "roofline": roof_for(kt, True),
+        "kernels": kt,
+        "fp64": {"value": v64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64["ms"] / fp64_steps,
+                 "dtype": "f64", "roofline": roof_for(kt64, False), "kernels": kt64,
+                 "clocks": fp64["clocks"]},
+        "error": {"mixed_vs_fp64_state_rel_l2": err, "after_steps": k_err,
+                  "fp64_vs_oracle": "<= 1e-12 relative L2 (parity tests)"},
+    }
+    if world > 1:
+        line["parallelism"] = f"{world} independent replicas (one full mesh per GPU)"
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        Qh = torch.from_numpy(np.ascontiguousarray(Q0)).pin_memory()
+        Qo = torch.empty_like(Qh).pin_memory()
+        e_steps = max(3, args.steps // 4)
+        S.set_state(Q0)
+        gks.gks_step(S.h, mixed["dt"], 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            gks.gks_set_state(S.h, Qh)
+            gks.gks_step(S.h, mixed["dt"], 1)
+            gks.gks_get_state(S.h, Qo)
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": nc * 2 * e_steps / el, "unit": UNIT, "steps": e_steps,
+                       "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Qo.numel() * 8),
+                       "api": "gks_set_state(host) + gks_step + gks_get_state(host)"}
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        n_s, steps_s, el_s, cores = time_oracle(16, 10.0)
+        line["cpu_baseline"] = {"value": n_s * 2 * steps_s / el_s, "unit": UNIT, "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{steps_s} S2O4 steps on the {n_s}-cell 16^3-cube mesh of the same generator"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

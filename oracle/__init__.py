@@ -54,8 +54,8 @@ def lib():
         L.oracle_mesh_create.restype = P
         L.oracle_mesh_create.argtypes = [ctypes.c_int64, D, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int8),
-                                         ctypes.POINTER(ctypes.c_int64), I, D, D, I,
-                                         ctypes.c_char_p, ctypes.c_int]
+                                         ctypes.POINTER(ctypes.c_int64), I, D, D, ctypes.c_int,
+                                         I, ctypes.c_char_p, ctypes.c_int]
         L.oracle_mesh_destroy.argtypes = [P]
         L.oracle_n_faces.restype = ctypes.c_int64
         L.oracle_n_faces.argtypes = [P]
@@ -68,6 +68,7 @@ def lib():
         L.oracle_slope.argtypes = [ctypes.c_double] * 5 + [D, D]
         L.oracle_residual.argtypes = [P, D, D, ctypes.c_double, D, D, ctypes.c_char_p, ctypes.c_int]
         L.oracle_residual_jvp.argtypes = [P, D, D, D, ctypes.c_double, D, D, D, D]
+        L.oracle_residual_cells.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int, I, D, D]
         L.oracle_step.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int]
         L.oracle_step_jvp.argtypes = [P, D, D, D, ctypes.c_double, ctypes.c_int]
         L.oracle_s2o4_stage1.argtypes = [ctypes.c_int64, D, D, D, ctypes.c_double, D]
@@ -94,7 +95,7 @@ class OracleError(RuntimeError):
 class Mesh:
     """The oracle's view of a mesh: topology, geometry and stencils built from the inputs."""
 
-    def __init__(self, mesh: dict):
+    def __init__(self, mesh: dict, lazy: bool = False):
         L = lib()
         xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
         ct = np.ascontiguousarray(mesh["cell_type"], dtype=np.int8)
@@ -107,7 +108,7 @@ class Mesh:
         self.h = L.oracle_mesh_create(len(xyz), _d(xyz), len(ct),
                                       ct.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                                       cn.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _i(bc),
-                                      _d(lo), _d(hi), ctypes.byref(st), err, 256)
+                                      _d(lo), _d(hi), 1 if lazy else 0, ctypes.byref(st), err, 256)
         if not self.h:
             raise OracleError(st.value, err.value.decode())
         self.n_cells = len(ct)
@@ -158,6 +159,16 @@ class Mesh:
         st = lib().oracle_residual(self.h, _d(params), _d(Q), dt, _d(L), _d(Lt), err, 256)
         if st:
             raise OracleError(st, err.value.decode())
+        return L, Lt
+
+    def residual_cells(self, params, Q, dt, cells):
+        """L and Lt [len(cells), 5] of the listed cells only."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        L, Lt = np.zeros((len(cells), 5)), np.zeros((len(cells), 5))
+        st = lib().oracle_residual_cells(self.h, _d(params), _d(Q), dt, len(cells), _i(cells), _d(L), _d(Lt))
+        if st:
+            raise OracleError(st)
         return L, Lt
 
     def residual_jvp(self, params, Q, dQ, dt):

@@ -340,6 +340,7 @@ struct Cell {
   QR qr0;
   std::vector<QR> qrm;
   bool plain = true;                      // no member carries a transform
+  bool ready = false;                     // stencil and least-squares systems built
 };
 struct Mesh {
   int n_nodes = 0, n_cells = 0;
@@ -416,7 +417,10 @@ const std::vector<SubDef>& sub_defs(int type) {
   return pyr;
 }
 
-int build_mesh(Mesh& m) {
+int build_cell_stencil(Mesh& m, int i);
+
+// Topology and geometry of all cells and faces; with lazy = false also every cell's stencils.
+int build_mesh(Mesh& m, bool lazy) {
   const double ext = std::max({m.L[0], m.L[1], m.L[2]});
   const double tol = 1e-9 * ext;
   // cells and their own quadrature
@@ -605,9 +609,21 @@ int build_mesh(Mesh& m) {
     }
     m.faces.push_back(f);
   }
-  // stencils, Section 2: neighbours, then neighbours of neighbours, as a set
+  if (lazy) return ST_OK;
   for (int i = 0; i < m.n_cells; ++i) {
+    const int st = build_cell_stencil(m, i);
+    if (st) return st;
+  }
+  return ST_OK;
+}
+
+// Stencils of cell i (Section 2): neighbours, then neighbours of neighbours, as a set; the
+// sub-stencils; and the least-squares systems of both.
+int build_cell_stencil(Mesh& m, int i) {
+  const double tol = 1e-9 * std::max({m.L[0], m.L[1], m.L[2]});
+  {
     Cell& ci = m.cells[i];
+    if (ci.ready) return ST_OK;
     auto add = [&](std::vector<Member>& list, const Member& mb) -> int {
       if (mb.cell == i && is_identity(mb.T, tol)) return -1;
       for (size_t k = 0; k < list.size(); ++k)
@@ -665,6 +681,7 @@ int build_mesh(Mesh& m) {
         return ST_SINGULAR;
       }
     }
+    ci.ready = true;
   }
   return ST_OK;
 }
@@ -1042,6 +1059,10 @@ void frame(const double* n1, double n2[3], double n3[3]) {
 // ---------------------------------------------------------------------------------------------
 // Residual L(Q) and its time derivative (Eq. finite with the two-point time fit).
 template <class T>
+bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& ro,
+               const Recon<T>* rn, double dt, T* out);
+
+template <class T>
 int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lto,
              std::string& err) {
   const int n = m.n_cells;
@@ -1063,17 +1084,45 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : bad)
   for (int f = 0; f < nf; ++f) {
     const Face& fc = m.faces[f];
+    if (!face_flux(m, P, fc, rec[fc.owner], fc.nb >= 0 ? &rec[fc.nb] : nullptr, dt, ff[f].data()))
+      ++bad;
+  }
+  if (bad) {
+    err = "non-physical reconstructed state at a Gauss point";
+    return ST_NONPHYS;
+  }
+  for (size_t k = 0; k < 5 * (size_t)n; ++k) Lo[k] = Lto[k] = T(0.0);
+  for (int f = 0; f < nf; ++f) {
+    const Face& fc = m.faces[f];
+    for (int v = 0; v < 5; ++v) {
+      Lo[v * (size_t)n + fc.owner] -= ff[f][v] / m.cells[fc.owner].vol;
+      Lto[v * (size_t)n + fc.owner] -= ff[f][5 + v] / m.cells[fc.owner].vol;
+      if (fc.nb >= 0) {
+        Lo[v * (size_t)n + fc.nb] += ff[f][v] / m.cells[fc.nb].vol;
+        Lto[v * (size_t)n + fc.nb] += ff[f][5 + v] / m.cells[fc.nb].vol;
+      }
+    }
+  }
+  return ST_OK;
+}
+
+// Face flux (Eq. flux-qud over the 2x2 Gauss points) fitted in time:
+// out[0..4] = F^n, out[5..9] = dF/dt. Returns false for a non-physical state.
+template <class T>
+bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& ro,
+               const Recon<T>* rn, double dt, T* out) {
+  {
     T acc[2][5];
     for (int s = 0; s < 2; ++s)
       for (int v = 0; v < 5; ++v) acc[s][v] = T(0.0);
     for (int k = 0; k < 4; ++k) {
       T vl[5], gl[5][3], vr[5], gr[5][3];
-      eval_recon(m, fc.owner, rec[fc.owner], fc.xg[k], vl, gl);
+      eval_recon(m, fc.owner, ro, fc.xg[k], vl, gl);
       if (fc.nb >= 0) {
         double xn[3];
         for (int a = 0; a < 3; ++a) xn[a] = (fc.xg[k][a] - fc.nb_to_owner.t[a]) / fc.nb_to_owner.s[a];
         T v0[5], g0[5][3];
-        eval_recon(m, fc.nb, rec[fc.nb], xn, v0, g0);
+        eval_recon(m, fc.nb, *rn, xn, v0, g0);
         transform_state(fc.nb_to_owner, v0, vr);
         for (int v = 0; v < 5; ++v) {
           const double sv = (v >= 1 && v <= 3 && fc.nb_to_owner.s[v - 1] < 0) ? -1.0 : 1.0;
@@ -1110,10 +1159,7 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
         rot(sr, dqr[d]);
       }
       T F[2][5];
-      if (!gp_flux(P, ql, dql, qr, dqr, dt, F)) {
-        ++bad;
-        continue;
-      }
+      if (!gp_flux(P, ql, dql, qr, dqr, dt, F)) return false;
       for (int s = 0; s < 2; ++s) {
         T g[5];
         g[0] = F[s][0];
@@ -1128,27 +1174,11 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
           if (v != 1 + fc.wall_axis) acc[s][v] = T(0.0);
     }
     for (int v = 0; v < 5; ++v) {
-      ff[f][v] = (4.0 * acc[0][v] - acc[1][v]) / dt;
-      ff[f][5 + v] = 4.0 * (acc[1][v] - 2.0 * acc[0][v]) / (dt * dt);
+      out[v] = (4.0 * acc[0][v] - acc[1][v]) / dt;
+      out[5 + v] = 4.0 * (acc[1][v] - 2.0 * acc[0][v]) / (dt * dt);
     }
   }
-  if (bad) {
-    err = "non-physical reconstructed state at a Gauss point";
-    return ST_NONPHYS;
-  }
-  for (size_t k = 0; k < 5 * (size_t)n; ++k) Lo[k] = Lto[k] = T(0.0);
-  for (int f = 0; f < nf; ++f) {
-    const Face& fc = m.faces[f];
-    for (int v = 0; v < 5; ++v) {
-      Lo[v * (size_t)n + fc.owner] -= ff[f][v] / m.cells[fc.owner].vol;
-      Lto[v * (size_t)n + fc.owner] -= ff[f][5 + v] / m.cells[fc.owner].vol;
-      if (fc.nb >= 0) {
-        Lo[v * (size_t)n + fc.nb] += ff[f][v] / m.cells[fc.nb].vol;
-        Lto[v * (size_t)n + fc.nb] += ff[f][5 + v] / m.cells[fc.nb].vol;
-      }
-    }
-  }
-  return ST_OK;
+  return true;
 }
 
 // Two-stage fourth-order update (Section 3.3).
@@ -1181,9 +1211,11 @@ int step(const Mesh& m, const Params& P, T* Q, double dt, int nsteps, std::strin
 // C entry points (used through ctypes by the tests).
 extern "C" {
 
+// lazy != 0 builds only topology and geometry; stencils are built on first use (for the
+// sampled residual on large meshes).
 void* oracle_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
                          const int8_t* cell_type, const int64_t* cell_nodes, const int* bc,
-                         const double* lo, const double* hi, int* status, char* errbuf,
+                         const double* lo, const double* hi, int lazy, int* status, char* errbuf,
                          int errlen) {
   Mesh* m = new Mesh;
   m->n_nodes = (int)n_nodes;
@@ -1200,7 +1232,7 @@ void* oracle_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
     m->cells[c].type = cell_type[c];
     for (int s = 0; s < 8; ++s) m->cells[c].node[s] = (int)cell_nodes[8 * c + s];
   }
-  *status = build_mesh(*m);
+  *status = build_mesh(*m, lazy != 0);
   if (*status) {
     if (errbuf && errlen > 0) {
       std::strncpy(errbuf, m->err.c_str(), errlen - 1);
@@ -1360,6 +1392,52 @@ int oracle_residual_jvp(void* h, const double* params, const double* Q, const do
     dL[k] = l[k].d;
     Lt[k] = lt[k].v;
     dLt[k] = lt[k].d;
+  }
+  return ST_OK;
+}
+
+// L and Lt of the listed cells only (out[p][5] each), for spot checks on large meshes.
+int oracle_residual_cells(void* h, const double* params, const double* Q, double dt, int ncells,
+                          const int* cells, double* L, double* Lt) {
+  Mesh* m = static_cast<Mesh*>(h);
+  const Params P = read_params(params);
+  const int n = m->n_cells;
+  std::map<int, Recon<double>> rec;
+  auto get = [&](int c) -> const Recon<double>& {
+    auto it = rec.find(c);
+    if (it != rec.end()) return it->second;
+    Recon<double>& r = rec[c];
+    reconstruct_cell(*m, P, Q, n, c, r);
+    return r;
+  };
+  for (int p = 0; p < ncells; ++p) {
+    const int i = cells[p];
+    if (i < 0 || i >= n) return ST_INVAL;
+    std::vector<int> need = {i};
+    for (int f : m->cells[i].face_id) {
+      need.push_back(m->faces[f].owner);
+      if (m->faces[f].nb >= 0) need.push_back(m->faces[f].nb);
+    }
+    for (int c : need) {
+      const int st = build_cell_stencil(*m, c);
+      if (st) return st;
+    }
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int f : m->cells[i].face_id) {
+      const Face& fc = m->faces[f];
+      double ff[10];
+      const Recon<double>& ro = get(fc.owner);
+      const Recon<double>* rn = fc.nb >= 0 ? &get(fc.nb) : nullptr;
+      if (!face_flux(*m, P, fc, ro, rn, dt, ff)) return ST_NONPHYS;
+      if (fc.owner == i)
+        for (int v = 0; v < 10; ++v) acc[v] -= ff[v];
+      if (fc.nb == i)
+        for (int v = 0; v < 10; ++v) acc[v] += ff[v];
+    }
+    for (int v = 0; v < 5; ++v) {
+      L[5 * p + v] = acc[v] / m->cells[i].vol;
+      Lt[5 * p + v] = acc[5 + v] / m->cells[i].vol;
+    }
   }
   return ST_OK;
 }

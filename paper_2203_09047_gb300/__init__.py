@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_timing_enable.restype = st
     L.gks_timing_read.argtypes = [P, D, ctypes.POINTER(I64)]
     L.gks_timing_read.restype = st
+    L.gks_kernel_bytes.argtypes = [P, D]
+    L.gks_kernel_bytes.restype = st
     L.gks_flux_opcount.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
     L.gks_flux_opcount.restype = ctypes.c_int
     L.gks_last_error.argtypes = [P]
@@ -194,6 +196,13 @@ def gks_timing_read(solver):
     return list(ms), list(cnt)
 
 
+def gks_kernel_bytes(solver):
+    """Algorithmic bytes per launch of (reconstruction, flux, face sum + update)."""
+    b = (ctypes.c_double * 3)()
+    _check(load_library().gks_kernel_bytes(solver, b), solver)
+    return list(b)
+
+
 def gks_flux_opcount(flux_mode: int, tau_model: int):
     """(flops, special-function calls) of one face Gauss point of the flux kernel."""
     f, sp = ctypes.c_double(), ctypes.c_double()
@@ -211,23 +220,44 @@ def gks_mesh_destroy(mesh):
 
 
 # ---------------------------------------------------------------------------- convenience
-class Solver:
-    """Owns a mesh handle and a solver handle; states are torch float64 tensors [5, n_cells]
-    on the solver's CUDA device (or pinned host tensors for host-side transfers)."""
+class Mesh:
+    """Owns a gks_mesh handle built from an inputs-style mesh dict (host-side topology only)."""
 
-    def __init__(self, mesh: dict, stream=None, **params):
+    def __init__(self, mesh: dict):
+        self.h = gks_mesh_create(mesh["xyz"], mesh["cell_type"], mesh["cell_nodes"], mesh["bc"],
+                                 mesh["lo"], mesh["hi"])
+        self.n_cells, self.n_faces, self.n_stencil = gks_mesh_counts(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gks_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """Owns a solver handle; states are torch float64 tensors [5, n_cells] on the solver's CUDA
+    device (or pinned host tensors for host-side transfers). `mesh` is an inputs-style dict or a
+    Mesh (which may be shared by several solvers)."""
+
+    def __init__(self, mesh, stream=None, **params):
         import torch
         self.torch = torch
-        self.mesh_h = gks_mesh_create(mesh["xyz"], mesh["cell_type"], mesh["cell_nodes"],
-                                      mesh["bc"], mesh["lo"], mesh["hi"])
-        self.n_cells, self.n_faces, self.n_stencil = gks_mesh_counts(self.mesh_h)
+        own = not isinstance(mesh, Mesh)
+        M = Mesh(mesh) if own else mesh
+        self.n_cells, self.n_faces, self.n_stencil = M.n_cells, M.n_faces, M.n_stencil
         self.params = gks_params_default(**params)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         try:
-            self.h = gks_init(self.mesh_h, self.params, self.stream.cuda_stream)
+            self.h = gks_init(M.h, self.params, self.stream.cuda_stream)
         finally:
-            gks_mesh_destroy(self.mesh_h)
-            self.mesh_h = None
+            if own:
+                M.close()
 
     def close(self):
         if getattr(self, "h", None):

@@ -438,6 +438,22 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
   return s->fail(GKS_E_INVAL, "the residual VJP is not available in this build");
 }
 
+gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
+  if (!s || !bytes) return GKS_E_INVAL;
+  const double nc = (double)s->m.nc, nf = (double)s->m.nf, nst = (double)s->m.nst,
+               nsb = (double)s->m.nsb, ncf = 2.0 * nf;  // each face appears in two cells
+  const double r = s->mixed ? 4.0 : 8.0;
+  // reconstruction: Q (own + stencil, once), CSR offsets, stencil entries and membership,
+  // pseudo-inverses, cell moments and size, polynomial coefficients written
+  bytes[0] = 40.0 * nc + 4.0 * (nc + 1) + nc + 4.0 * (nc + 1) + 5.0 * nst + 9.0 * r * nst +
+             3.0 * r * nsb + 7.0 * r * nc + 50.0 * r * nc;
+  // flux: face cells and wall flag, Gauss data, polynomials read, face fluxes written
+  bytes[1] = 9.0 * nf + 40.0 * r * nf + 50.0 * r * nc + 10.0 * r * nf;
+  // face sums + stage update: CSR, face fluxes, volumes, Q^n read, L/Lt and the stage state
+  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + 10.0 * r * nf + 8.0 * nc + 160.0 * nc;
+  return GKS_OK;
+}
+
 gks_status gks_timing_enable(gks_solver* s, int enable) {
   if (!s) return GKS_E_INVAL;
   s->timing = enable != 0;
