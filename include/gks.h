@@ -164,7 +164,30 @@ gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]);
  * scalar type. Returns 0 on success. Not thread-safe. */
 int gks_flux_opcount(int flux_mode, int tau_model, double* flops, double* special);
 
-/* Text of the solver's last error. */
+/* Allocation-free CFL time-step bound, for callers that cannot call cudaMalloc: processes
+ * whose device memory is owned by another allocator (a framework pool that has reserved the
+ * device) or latency-critical loops that must not pay for cudaMalloc's implicit device
+ * synchronisation. The paper has no counterpart; it is the time-step reduction of gks_max_dt
+ * written as a stand-alone call whose scratch is a fixed array inside the library.
+ *   n_cells  number of cells, at most 16,777,216 (65,536 blocks of 256 cells: the scratch holds
+ *            one 8-byte partial minimum per block, 512 KiB per device); larger n is rejected with
+ *            GKS_E_INVAL and a message in gks_last_error(NULL).
+ *   Q        device pointer, float64 [5][n_cells] conserved variables (any cell order).
+ *   h        device pointer, float64 [n_cells] length of each cell in the same order (the solver
+ *            uses |Omega_i| / largest face area).
+ *   dt       device pointer to one float64: receives cfl * min_i h_i / (|U_i| + c_i +
+ *            2 mu / (rho_i h_i)), or -1 if any cell has rho <= 0, p <= 0 or NaN.
+ *   stream   cudaStream_t on which both kernels are enqueued; the call does not synchronise.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. The first call on a device
+ * looks up the device address of the scratch array (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call on a device shares the
+ * one scratch array, so calls whose kernels overlap on the GPU (different streams, no ordering)
+ * race on it; order them on one stream. Returns GKS_OK once both kernels are enqueued. */
+gks_status gks_cfl_dt_noalloc(int64_t n_cells, const double* Q, const double* h, double gamma,
+                              double mu, double cfl, double* dt, void* stream);
+
+/* Text of the solver's last error (s = NULL: the last mesh-construction or stand-alone-call
+ * error on this thread). */
 const char* gks_last_error(const gks_solver* s);
 
 void gks_destroy(gks_solver* s);

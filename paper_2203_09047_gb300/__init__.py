@@ -86,6 +86,9 @@ def load_library(path: str = LIB_PATH):
     L.gks_kernel_bytes.restype = st
     L.gks_flux_opcount.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
     L.gks_flux_opcount.restype = ctypes.c_int
+    L.gks_cfl_dt_noalloc.argtypes = [I64, P, P, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, P, P]
+    L.gks_cfl_dt_noalloc.restype = st
     L.gks_last_error.argtypes = [P]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_destroy.argtypes = [P]
@@ -209,6 +212,16 @@ def gks_flux_opcount(flux_mode: int, tau_model: int):
     if load_library().gks_flux_opcount(flux_mode, tau_model, ctypes.byref(f), ctypes.byref(sp)):
         raise GksError(GKS_E_NONPHYSICAL, "op count failed")
     return f.value, sp.value
+
+
+def gks_cfl_dt_noalloc(n_cells: int, Q, h, gamma: float, mu: float, cfl: float, dt_out,
+                       stream: int = 0):
+    """Allocation-free CFL bound: Q [5, n] and h [n] device float64, dt_out a device float64[1]."""
+    L = load_library()
+    s = L.gks_cfl_dt_noalloc(n_cells, _ptr(Q), _ptr(h), gamma, mu, cfl, _ptr(dt_out),
+                             ctypes.c_void_p(stream))
+    if s != GKS_OK:
+        raise GksError(s, L.gks_last_error(None).decode())
 
 
 def gks_destroy(solver):

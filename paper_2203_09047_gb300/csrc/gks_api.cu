@@ -29,6 +29,8 @@ cudaError_t upload(T** p, const std::vector<T>& v, cudaStream_t st) {
 }
 }  // namespace
 
+void gks::set_global_error(const char* msg) { g_mesh_err = msg ? msg : ""; }
+
 struct gks_solver {
   gks_params prm;
   cudaStream_t st = nullptr;

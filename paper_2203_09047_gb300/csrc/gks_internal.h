@@ -56,6 +56,8 @@ struct gks_mesh {
 };
 
 namespace gks {
+// Set the text returned by gks_last_error(NULL) / gks_mesh_last_error() on this thread.
+void set_global_error(const char* msg);
 // Host mesh construction (gks_mesh.cpp). Returns a status and fills err.
 gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
                            const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
