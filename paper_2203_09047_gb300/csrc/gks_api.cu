@@ -47,8 +47,10 @@ struct gks_solver {
   double* Lt = nullptr;
   double* tmp = nullptr;    // staging in caller order [5][nc]
   double* tmp2 = nullptr;   // second staging buffer
-  void* poly = nullptr;     // [50][nc] in R
-  void* fface = nullptr;    // [10][nf] in R
+  void* poly = nullptr;     // [nc][kPolyStride] in R
+  void* fface = nullptr;    // [nf][kFaceStride] in R
+  void* QA = nullptr;       // gather copy of Q (Lay<R>::gq values per cell)
+  void* QsA = nullptr;      // gather copy of the stage state
   int* flag = nullptr;      // device status bits
   int* bad_cell = nullptr;
   double* dt_part = nullptr;
@@ -127,17 +129,24 @@ template <class R>
 gks_status alloc_geo(gks_solver* s, GeoR<R>& g) {
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e;
-  if ((e = salloc(s, &g.Ap, 9 * s->m.nst)) != cudaSuccess) return s->cuda_fail(e, "alloc A+");
-  if ((e = salloc(s, &g.Bp, 3 * s->m.nsb)) != cudaSuccess) return s->cuda_fail(e, "alloc B");
+  if ((e = salloc(s, &g.Ap, (int64_t)Lay<R>::apad * s->m.nst)) != cudaSuccess)
+    return s->cuda_fail(e, "alloc A+");
+  if ((e = salloc(s, &g.Bp, 4 * s->m.nsb)) != cudaSuccess) return s->cuda_fail(e, "alloc B");
   if ((e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc moments");
   if ((e = salloc(s, &g.h, nc)) != cudaSuccess) return s->cuda_fail(e, "alloc h");
   if ((e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face data");
   R* poly = nullptr;
   R* ff = nullptr;
-  if ((e = salloc(s, &poly, 50 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc poly");
-  if ((e = salloc(s, &ff, 10 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face flux");
+  R* qa = nullptr;
+  R* qsa = nullptr;
+  if ((e = salloc(s, &poly, (int64_t)kPolyStride * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc poly");
+  if ((e = salloc(s, &ff, (int64_t)kFaceStride * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face flux");
+  if ((e = salloc(s, &qa, (int64_t)Lay<R>::gq * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
+  if ((e = salloc(s, &qsa, (int64_t)Lay<R>::gq * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
   s->poly = poly;
   s->fface = ff;
+  s->QA = qa;
+  s->QsA = qsa;
   return GKS_OK;
 }
 
@@ -149,29 +158,37 @@ void precompute_r(gks_solver* s, GeoR<R>& g) {
   launch_cast_cells<R>(s->m, s->g, g, s->st);
 }
 
-// One residual evaluation on internal-order state Qin: recon -> flux -> gather(mode).
+// One residual evaluation: recon (from the gather copy QinA) -> flux -> gather(mode).
 template <class R>
-void residual_r(gks_solver* s, GeoR<R>& g, const double* Qin, double dt, int mode, double* L,
+void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode, double* L,
                 double* Lt, double* Qn, double* Qs) {
   const KParams<R> kp = kparams<R>(s->prm);
   int t = s->tick(0);
-  launch_recon<R>(s->m, g, kp, Qin, (R*)s->poly, s->st);
+  launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->st);
   s->tock(t);
   t = s->tick(1);
   launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
   s->tock(t);
   t = s->tick(2);
-  launch_gather<R>(s->m, s->g, (const R*)s->fface, mode, dt, s->prm.gamma, L, Lt, Qn, Qs, s->flag,
-                   s->st);
+  launch_gather<R>(s->m, s->g, (const R*)s->fface, mode, dt, s->prm.gamma, L, Lt, Qn, Qs,
+                   (R*)s->QA, (R*)s->QsA, s->flag, s->st);
   s->tock(t);
 }
 
-void residual_any(gks_solver* s, const double* Qin, double dt, int mode, double* L, double* Lt,
+void residual_any(gks_solver* s, const void* QinA, double dt, int mode, double* L, double* Lt,
                   double* Qn, double* Qs) {
   if (s->mixed)
-    residual_r<float>(s, s->gf, Qin, dt, mode, L, Lt, Qn, Qs);
+    residual_r<float>(s, s->gf, QinA, dt, mode, L, Lt, Qn, Qs);
   else
-    residual_r<double>(s, s->gd, Qin, dt, mode, L, Lt, Qn, Qs);
+    residual_r<double>(s, s->gd, QinA, dt, mode, L, Lt, Qn, Qs);
+}
+
+// Caller-order state -> internal order (dst) and its gather copy (gq).
+void permute_in_any(gks_solver* s, const double* src, double* dst, void* gq) {
+  if (s->mixed)
+    launch_permute_in<float>(s->m.nc, s->m.perm, src, dst, (float*)gq, s->st);
+  else
+    launch_permute_in<double>(s->m.nc, s->m.perm, src, dst, (double*)gq, s->st);
 }
 
 gks_status read_flag(gks_solver* s, int* out) {
@@ -307,6 +324,7 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.st_sub, h.st_sub)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.n_sub, h.n_sub)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.sb_ptr, h.sb_ptr)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.sub_cnt, h.sub_cnt)) != cudaSuccess) return bad("upload");
   const int64_t nc = m.nc, nf = m.nf;
   if ((e = salloc(s, &s->g.vol, nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.cen, 3 * nc)) != cudaSuccess) return bad("alloc");
@@ -364,7 +382,7 @@ gks_status gks_set_state(gks_solver* s, const double* Q) {
   const int64_t nc = s->m.nc;
   cudaError_t e = cudaMemcpyAsync(s->tmp, Q, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
   if (e != cudaSuccess) return s->cuda_fail(e, "set_state copy");
-  launch_permute_in(nc, s->m.perm, s->tmp, s->Q, s->st);
+  permute_in_any(s, s->tmp, s->Q, s->QA);
   e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "set_state");
 }
@@ -397,8 +415,8 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps) {
   if (!s || !(dt > 0) || nsteps < 0) return GKS_E_INVAL;
   for (int k = 0; k < nsteps; ++k) {
     // stage 1 on Q^n: L, Lt kept, Qs = Q* ; stage 2 on Q*: Q^{n+1} written into Q
-    residual_any(s, s->Q, dt, 1, s->L, s->Lt, s->Q, s->Qs);
-    residual_any(s, s->Qs, dt, 2, s->L, s->Lt, s->Q, s->Qs);
+    residual_any(s, s->QA, dt, 1, s->L, s->Lt, s->Q, s->Qs);
+    residual_any(s, s->QsA, dt, 2, s->L, s->Lt, s->Q, s->Qs);
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
@@ -414,9 +432,9 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
   const int64_t nc = s->m.nc;
   cudaError_t e = cudaMemcpyAsync(s->tmp, Q, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
   if (e != cudaSuccess) return s->cuda_fail(e, "residual copy");
-  launch_permute_in(nc, s->m.perm, s->tmp, s->Qs, s->st);
+  permute_in_any(s, s->tmp, s->Qs, s->QsA);
   launch_check_state(nc, s->Qs, s->prm.gamma, s->flag, s->st);
-  residual_any(s, s->Qs, dt, 0, s->tmp, s->tmp2, nullptr, nullptr);
+  residual_any(s, s->QsA, dt, 0, s->tmp, s->tmp2, nullptr, nullptr);
   // tmp, tmp2 hold L, Lt in internal order; write them out in caller order
   launch_permute_out(nc, s->m.perm, s->tmp, s->Qs, s->st);
   e = cudaMemcpyAsync(L, s->Qs, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
@@ -445,14 +463,17 @@ gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
   const double nc = (double)s->m.nc, nf = (double)s->m.nf, nst = (double)s->m.nst,
                nsb = (double)s->m.nsb, ncf = 2.0 * nf;  // each face appears in two cells
   const double r = s->mixed ? 4.0 : 8.0;
-  // reconstruction: Q (own + stencil, once), CSR offsets, stencil entries and membership,
-  // pseudo-inverses, cell moments and size, polynomial coefficients written
-  bytes[0] = 40.0 * nc + 4.0 * (nc + 1) + nc + 4.0 * (nc + 1) + 5.0 * nst + 9.0 * r * nst +
-             3.0 * r * nsb + 7.0 * r * nc + 50.0 * r * nc;
+  const double ap = s->mixed ? Lay<float>::apad : Lay<double>::apad;
+  // reconstruction: gather copy of Q (48 B per cell, own + stencil, once), CSR offsets and
+  // counts, stencil entries, pseudo-inverse rows, sub-stencil entries, cell moments and size,
+  // polynomial coefficients written
+  bytes[0] = 48.0 * nc + 4.0 * (nc + 1) + nc + 4.0 * (nc + 1) + 8.0 * nc + 4.0 * nst +
+             ap * r * nst + 4.0 * r * nsb + 7.0 * r * nc + kPolyStride * r * nc;
   // flux: face cells and wall flag, Gauss data, polynomials read, face fluxes written
-  bytes[1] = 9.0 * nf + 40.0 * r * nf + 50.0 * r * nc + 10.0 * r * nf;
-  // face sums + stage update: CSR, face fluxes, volumes, Q^n read, L/Lt and the stage state
-  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + 10.0 * r * nf + 8.0 * nc + 160.0 * nc;
+  bytes[1] = 9.0 * nf + 40.0 * r * nf + kPolyStride * r * nc + kFaceStride * r * nf;
+  // face sums + stage update: CSR, face fluxes, volumes, Q^n read, L/Lt and the stage state,
+  // the gather copy of the new state
+  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + kFaceStride * r * nf + 8.0 * nc + 160.0 * nc + 48.0 * nc;
   return GKS_OK;
 }
 

@@ -10,6 +10,27 @@
 
 namespace gks {
 
+// Storage layouts of the hot path.
+//  - gather copy of the state, 48 bytes per cell: FP32 path [hi0..hi4, lo0..lo4, 0, 0] with
+//    hi = (float)q and lo = (float)(q - hi); FP64 path [q0..q4, 0];
+//  - pseudo-inverse rows: one row of Lay<R>::apad values per stencil member (9 used);
+//  - sub-stencil entries: 4 values {B_0k, B_1k, B_2k, k} per (sub-stencil, member), sub-stencil
+//    major within a cell;
+//  - cell polynomials: kPolyStride values per cell, variable v at offset 10 v;
+//  - face fluxes: kFaceStride values per face (F^n 0..4, dF/dt 5..9).
+template <class R>
+struct Lay;
+template <>
+struct Lay<float> {
+  static constexpr int apad = 12, gq = 12;
+};
+template <>
+struct Lay<double> {
+  static constexpr int apad = 10, gq = 6;
+};
+constexpr int kPolyStride = 52;
+constexpr int kFaceStride = 12;
+
 // Error bits of the device status word.
 enum : int {
   kErrInverted = 1,     // a cell Jacobian <= 0 at a quadrature point
@@ -37,6 +58,7 @@ struct DevMesh {
   uint8_t* st_sub = nullptr;
   int8_t* n_sub = nullptr;
   int32_t* sb_ptr = nullptr;
+  uint64_t* sub_cnt = nullptr;
 };
 
 // FP64 geometry (always kept).
@@ -52,8 +74,8 @@ struct Geo64 {
 // Geometry in the arithmetic precision R of the hot path.
 template <class R>
 struct GeoR {
-  R* Ap = nullptr;   // per cell a block [9][K] (row n over the K stencil members)
-  R* Bp = nullptr;   // per (member, sub-stencil) pair: 3 coefficients, member-major order
+  R* Ap = nullptr;   // per stencil member a row of Lay<R>::apad values (9 used)
+  R* Bp = nullptr;   // per (sub-stencil, member) pair: {3 coefficients, member index}
   R* mom = nullptr;  // [6][nc]
   R* h = nullptr;    // [nc]
   R* fgp = nullptr;  // [10][4 nf]: dl(3) dr(3) n1(3) w, index 4 f + gauss point
@@ -81,18 +103,21 @@ void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream
 
 // ---- hot path (gks_hot.cu) ----------------------------------------------------------------
 template <class R>
-void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const double* Q,
+void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                   R* poly, cudaStream_t st);
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
                  double dt, R* fface, int* flag, cudaStream_t st);
 // mode 0: write L, Lt. mode 1: stage 1 (store L, Lt; Qs = Qn + dt/2 L + dt^2/8 Lt).
 // mode 2: stage 2 (Qn += dt L0 + dt^2/6 (Lt0 + 2 Lt)).
+// The stage kernels also write the gather copy of the state they produce (QA for mode 2,
+// QsA for mode 1).
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
-                   double gamma, double* L, double* Lt, double* Qn, double* Qs, int* flag,
-                   cudaStream_t st);
-void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst,
+                   double gamma, double* L, double* Lt, double* Qn, double* Qs, R* QA, R* QsA,
+                   int* flag, cudaStream_t st);
+template <class R>
+void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst, R* gq,
                        cudaStream_t st);
 void launch_permute_out(int64_t nc, const int32_t* perm, const double* src, double* dst,
                         cudaStream_t st);

@@ -222,9 +222,10 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
       A[k + (3 + q) * K] = d[pa[q]] * d[pb[q]] + mj * r2 - m0[q];
     }
   }
-  // sub-stencils first (they only need the linear columns)
+  // sub-stencils first (they only need the linear columns); entries sub-stencil major
   const int M = n_sub[i];
   const int b0 = sb_ptr[i];
+  int pos = 0;
   for (int s = 0; s < M; ++s) {
     double S[kMaxStencil * 3];
     int idx[kMaxStencil];
@@ -242,11 +243,10 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
     for (int r = 0; r < km; ++r) {
       double out[3];
       pinv_column(S, km, 3, sb, srd, r, x, out);
-      const int k = idx[r];
-      int pos = 0;  // pairs before (k, s) in member-major order
-      for (int kk = 0; kk < k; ++kk) pos += __popc(st_sub[s0 + kk]);
-      pos += __popc(st_sub[s0 + k] & ((1u << s) - 1u));
-      for (int a = 0; a < 3; ++a) Bp[3 * (int64_t)(b0 + pos) + a] = (R)out[a];
+      R* e = Bp + 4 * (int64_t)(b0 + pos);
+      for (int a = 0; a < 3; ++a) e[a] = (R)out[a];
+      e[3] = (R)idx[r];  // member index, exact in either precision
+      ++pos;
     }
   }
   if (!qr_inplace(A, K, 9, beta, rd)) {
@@ -254,10 +254,12 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
     atomicMin(bad_cell, (int)i);
     return;
   }
-  R* Ai = Ap + 9 * (int64_t)s0;
+  constexpr int ap = Lay<R>::apad;
   for (int k = 0; k < K; ++k) {
     pinv_column(A, K, 9, beta, rd, k, x, col);
-    for (int n = 0; n < 9; ++n) Ai[n * K + k] = (R)col[n];
+    R* row = Ap + (int64_t)ap * (s0 + k);
+    for (int n = 0; n < 9; ++n) row[n] = (R)col[n];
+    for (int n = 9; n < ap; ++n) row[n] = R(0);
   }
 }
 

@@ -15,128 +15,290 @@ namespace {
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------------------------------
-// Reconstruction: one thread per cell, one pass per conserved variable. For variable v:
-//   dq_k = Q_k - Q_0 over the big stencil (formed in FP64, mirrored momentum sign-flipped),
-//   a    = A+ dq            (quadratic P0, 9 coefficients in centred scaled coordinates)
-//   b_m  = B_m dq|S_m       (linear P_m, 3 coefficients each)
-//   beta_0, beta_m (Eq. indicator), tau, omega, omega-bar (Section 2),
-//   C    = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m    (Eq. weno as one polynomial),
-// written as 10 coefficients of the polynomial in physical offsets from the centroid.
+// Gather copy of a state (48 bytes per cell, see Lay<R>) and the stencil differences taken
+// from it. FP32 path: each value is kept as hi + lo floats, so Q_k - Q_0 is formed as
+// (hi_k - hi_0) + (lo_k - lo_0) without FP64 arithmetic and is as accurate as rounding the
+// FP64 difference to FP32. FP64 path: the FP64 values themselves.
+template <class R>
+struct Gq;
+template <>
+struct Gq<float> {
+  float hi[5], lo[5];
+  __device__ __forceinline__ void load(const float* __restrict__ QA, int64_t c) {
+    const float4* p = reinterpret_cast<const float4*>(QA + 12 * c);
+    const float4 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2);
+    hi[0] = a.x; hi[1] = a.y; hi[2] = a.z; hi[3] = a.w; hi[4] = b.x;
+    lo[0] = b.y; lo[1] = b.z; lo[2] = b.w; lo[3] = d.x; lo[4] = d.y;
+  }
+  __device__ __forceinline__ void flip(int v) { hi[v] = -hi[v]; lo[v] = -lo[v]; }
+  __device__ __forceinline__ float minus(const Gq& c, int v) const {
+    return (hi[v] - c.hi[v]) + (lo[v] - c.lo[v]);
+  }
+  __device__ __forceinline__ float value(int v) const { return hi[v] + lo[v]; }
+  __device__ __forceinline__ float value_minus(int v, float x) const { return hi[v] + (lo[v] - x); }
+  __device__ static void store(float* QA, int64_t c, const double q[5]) {
+    float h[5], l[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      h[v] = (float)q[v];
+      l[v] = (float)(q[v] - (double)h[v]);
+    }
+    float4* p = reinterpret_cast<float4*>(QA + 12 * c);
+    p[0] = make_float4(h[0], h[1], h[2], h[3]);
+    p[1] = make_float4(h[4], l[0], l[1], l[2]);
+    p[2] = make_float4(l[3], l[4], 0.f, 0.f);
+  }
+};
+template <>
+struct Gq<double> {
+  double q[5];
+  __device__ __forceinline__ void load(const double* __restrict__ QA, int64_t c) {
+    const double2* p = reinterpret_cast<const double2*>(QA + 6 * c);
+    const double2 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2);
+    q[0] = a.x; q[1] = a.y; q[2] = b.x; q[3] = b.y; q[4] = d.x;
+  }
+  __device__ __forceinline__ void flip(int v) { q[v] = -q[v]; }
+  __device__ __forceinline__ double minus(const Gq& c, int v) const { return q[v] - c.q[v]; }
+  __device__ __forceinline__ double value(int v) const { return q[v]; }
+  __device__ __forceinline__ double value_minus(int v, double x) const { return q[v] - x; }
+  __device__ static void store(double* QA, int64_t c, const double qq[5]) {
+    double2* p = reinterpret_cast<double2*>(QA + 6 * c);
+    p[0] = make_double2(qq[0], qq[1]);
+    p[1] = make_double2(qq[2], qq[3]);
+    p[2] = make_double2(qq[4], 0.0);
+  }
+};
+
+// dq[v] = Q_member - Q_0 for one stencil entry (cell | mirrored-axis bits).
+template <class R>
+__device__ __forceinline__ void stencil_delta(const R* __restrict__ QA, int32_t e, const Gq<R>& c0,
+                                              R dq[5]) {
+  Gq<R> g;
+  g.load(QA, e & kCellMask);
+  const int fl = e >> kFlipShift;
+  if (fl & 1) g.flip(1);
+  if (fl & 2) g.flip(2);
+  if (fl & 4) g.flip(3);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dq[v] = g.minus(c0, v);
+}
+
+template <class R>
+__device__ __forceinline__ void load_row9(const R* __restrict__ p, R r[9]);
+template <>
+__device__ __forceinline__ void load_row9<float>(const float* __restrict__ p, float r[9]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+  r[8] = c.x;
+}
+template <>
+__device__ __forceinline__ void load_row9<double>(const double* __restrict__ p, double r[9]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldg(q + k);
+    r[2 * k] = a.x;
+    r[2 * k + 1] = a.y;
+  }
+  r[8] = __ldg(p + 8);
+}
+template <class R>
+__device__ __forceinline__ void load_entry(const R* __restrict__ p, R e[3], int& k);
+template <>
+__device__ __forceinline__ void load_entry<float>(const float* __restrict__ p, float e[3], int& k) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  e[0] = a.x; e[1] = a.y; e[2] = a.z;
+  k = (int)a.w;
+}
+template <>
+__device__ __forceinline__ void load_entry<double>(const double* __restrict__ p, double e[3], int& k) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  e[0] = a.x; e[1] = a.y; e[2] = b.x;
+  k = (int)b.y;
+}
+
+// ------------------------------------------------------------------------------------------
+// Reconstruction: one thread per cell, all five conserved variables at once.
+//   pass 1 over the big stencil:  a   = A+ dq           (quadratic P0, 9 coefficients per variable
+//                                                        in centred scaled coordinates)
+//   pass 2 over the sub-stencils: b_m = B_m dq|S_m      -> beta_m (Eq. indicator)
+//   weights (Section 2): tau, omega, omega-bar; the combination of Eq. weno as one polynomial
+//     C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m,
+//   pass 3 over the sub-stencils accumulates sum_m (...) b_m without storing the b_m.
+// Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
 template <class R>
 __global__ void __launch_bounds__(128) k_recon(
-    int64_t nc, const double* __restrict__ Q, const int32_t* __restrict__ st_ptr,
-    const int32_t* __restrict__ st_idx, const uint8_t* __restrict__ st_sub,
-    const int8_t* __restrict__ n_sub, const int32_t* __restrict__ sb_ptr,
+    int64_t nc, const R* __restrict__ QA, const int32_t* __restrict__ st_ptr,
+    const int32_t* __restrict__ st_idx, const int8_t* __restrict__ n_sub,
+    const int32_t* __restrict__ sb_ptr, const uint64_t* __restrict__ sub_cnt,
     const R* __restrict__ Ap, const R* __restrict__ Bp, const R* __restrict__ mom,
     const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
+  constexpr int ap = Lay<R>::apad;
   const int s0 = st_ptr[i];
   const int K = st_ptr[i + 1] - s0;
   const int M = n_sub[i];
-  const R* A = Ap + 9 * (int64_t)s0;
-  const R* B = Bp + 3 * (int64_t)sb_ptr[i];
+  const uint64_t cnt = sub_cnt[i];
+  const R* Bc = Bp + 4 * (int64_t)sb_ptr[i];
+  const int32_t* sidx = st_idx + s0;
+  Gq<R> c0;
+  c0.load(QA, i);
+  // pass 1: big-stencil least squares
+  R a[9][5];
+#pragma unroll
+  for (int n = 0; n < 9; ++n)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) a[n][v] = R(0);
+  for (int k = 0; k < K; ++k) {
+    R dq[5], row[9];
+    stencil_delta(QA, __ldg(sidx + k), c0, dq);
+    load_row9(Ap + (int64_t)ap * (s0 + k), row);
+#pragma unroll
+    for (int n = 0; n < 9; ++n)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) a[n][v] += row[n] * dq[v];
+  }
   R m2[6];
 #pragma unroll
   for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + i];
-  const R h = hcell[i];
-  const R ih = R(1) / h, ih2 = ih * ih;
-  const R g0 = R(1) - wg * R(M);
+  // beta_0: |l| = 1 terms are cell means of the squared first derivatives (linear in the scaled
+  // coordinates y, second moments m2), |l| = 2 terms the squared second derivatives
+  R beta0[5];
+#pragma unroll
   for (int v = 0; v < 5; ++v) {
-    const double q0 = Q[v * nc + i];
-    R a[9], b[kMaxSub][3];
-#pragma unroll
-    for (int n = 0; n < 9; ++n) a[n] = R(0);
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s) b[s][0] = b[s][1] = b[s][2] = R(0);
-    int bp = 0;
-    for (int k = 0; k < K; ++k) {
-      const int32_t e = st_idx[s0 + k];
-      double qk = Q[v * nc + (e & kCellMask)];
-      if (v >= 1 && v <= 3 && ((e >> (kFlipShift + v - 1)) & 1)) qk = -qk;
-      const R d = (R)(qk - q0);
-#pragma unroll
-      for (int n = 0; n < 9; ++n) a[n] += A[n * K + k] * d;
-      const unsigned sm = st_sub[s0 + k];
-#pragma unroll
-      for (int s = 0; s < kMaxSub; ++s) {
-        if (sm >> s & 1u) {
-          b[s][0] += B[bp] * d;
-          b[s][1] += B[bp + 1] * d;
-          b[s][2] += B[bp + 2] * d;
-          bp += 3;
-        }
-      }
-    }
-    // smoothness indicators in scaled coordinates: |l|=1 terms are cell means of the squared
-    // first derivatives (linear in y), |l|=2 terms are the squared second derivatives
-    const R gx[3] = {R(2) * a[3], a[6], a[7]};
-    const R gy[3] = {a[6], R(2) * a[4], a[8]};
-    const R gz[3] = {a[7], a[8], R(2) * a[5]};
-    auto qform = [&](const R g[3]) {
+    const R gx[3] = {R(2) * a[3][v], a[6][v], a[7][v]};
+    const R gy[3] = {a[6][v], R(2) * a[4][v], a[8][v]};
+    const R gz[3] = {a[7][v], a[8][v], R(2) * a[5][v]};
+    auto qf = [&](const R g[3]) {
       return m2[0] * g[0] * g[0] + m2[1] * g[1] * g[1] + m2[2] * g[2] * g[2] +
              R(2) * (m2[3] * g[0] * g[1] + m2[4] * g[0] * g[2] + m2[5] * g[1] * g[2]);
     };
-    const R beta0 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + qform(gx) + qform(gy) + qform(gz) +
-                    R(4) * (a[3] * a[3] + a[4] * a[4] + a[5] * a[5]) + a[6] * a[6] + a[7] * a[7] +
-                    a[8] * a[8];
-    R beta[kMaxSub];
-    R tau = R(0);
+    beta0[v] = a[0][v] * a[0][v] + a[1][v] * a[1][v] + a[2][v] * a[2][v] + qf(gx) + qf(gy) +
+               qf(gz) + R(4) * (a[3][v] * a[3][v] + a[4][v] * a[4][v] + a[5][v] * a[5][v]) +
+               a[6][v] * a[6][v] + a[7][v] * a[7][v] + a[8][v] * a[8][v];
+  }
+  // pass 2: sub-stencil fits and their indicators
+  R bet[kMaxSub][5];
+  {
+    const R* e = Bc;
 #pragma unroll
     for (int s = 0; s < kMaxSub; ++s) {
-      beta[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
-      if (s < M) tau += fabs(beta0 - beta[s]);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) bet[s][v] = R(0);
+      if (s < M) {
+        R b[3][5];
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+#pragma unroll
+          for (int v = 0; v < 5; ++v) b[t][v] = R(0);
+        const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+        for (int j = 0; j < cs; ++j, e += 4) {
+          R coef[3], dq[5];
+          int k;
+          load_entry(e, coef, k);
+          stencil_delta(QA, __ldg(sidx + k), c0, dq);
+#pragma unroll
+          for (int t = 0; t < 3; ++t)
+#pragma unroll
+            for (int v = 0; v < 5; ++v) b[t][v] += coef[t] * dq[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) bet[s][v] = b[0][v] * b[0][v] + b[1][v] * b[1][v] + b[2][v] * b[2][v];
+      }
     }
+  }
+  // nonlinear weights; bet[s][v] is overwritten by the sub-stencil factor of the combination
+  const R g0 = R(1) - wg * R(M);
+  R ca[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    R tau = R(0);
+#pragma unroll
+    for (int s = 0; s < kMaxSub; ++s)
+      if (s < M) tau += fabs(beta0[v] - bet[s][v]);
     tau /= R(M);
-    auto weight = [&](R gam, R bet) {
-      const R r = tau / (bet + weps);
-      R p = r;
-      for (int e = 1; e < wpow; ++e) p *= r;
-      return gam * (R(1) + p);
+    auto weight = [&](R gam, R bb) {
+      const R r = tau / (bb + weps);
+      R pw = r;
+      for (int q = 1; q < wpow; ++q) pw *= r;
+      return gam * (R(1) + pw);
     };
-    const R w0 = weight(g0, beta0);
-    R w[kMaxSub];
+    const R w0 = weight(g0, beta0[v]);
     R sum = w0;
 #pragma unroll
     for (int s = 0; s < kMaxSub; ++s) {
-      w[s] = s < M ? weight(wg, beta[s]) : R(0);
-      sum += w[s];
+      if (s < M) {
+        bet[s][v] = weight(wg, bet[s][v]);
+        sum += bet[s][v];
+      }
     }
     const R is = R(1) / sum;
     const R wb0 = w0 * is;
-    const R c_a = wb0 / g0;
-    R C[9];
+    ca[v] = wb0 / g0;
+    const R corr = wb0 * wg / g0;
 #pragma unroll
-    for (int n = 0; n < 9; ++n) C[n] = c_a * a[n];
+    for (int s = 0; s < kMaxSub; ++s)
+      if (s < M) bet[s][v] = bet[s][v] * is - corr;
+  }
+  // pass 3: linear part of the combination, sum_m cs_m b_m
+  R cl[3][5];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int v = 0; v < 5; ++v) cl[t][v] = R(0);
+  {
+    const R* e = Bc;
 #pragma unroll
     for (int s = 0; s < kMaxSub; ++s) {
       if (s < M) {
-        const R cs = w[s] * is - wb0 * wg / g0;
-        C[0] += cs * b[s][0];
-        C[1] += cs * b[s][1];
-        C[2] += cs * b[s][2];
+        const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+        for (int j = 0; j < cs; ++j, e += 4) {
+          R coef[3], dq[5];
+          int k;
+          load_entry(e, coef, k);
+          stencil_delta(QA, __ldg(sidx + k), c0, dq);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const R w = bet[s][v] * dq[v];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) cl[t][v] += coef[t] * w;
+          }
+        }
       }
     }
-    // polynomial in physical offsets d = x - centroid:
-    //   Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
-    const R c0 = (R)q0 - (C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] +
-                          C[7] * m2[4] + C[8] * m2[5]);
-    R* out = poly + (int64_t)(10 * v) * nc + i;
-    out[0] = c0;
-    out[1 * nc] = C[0] * ih;
-    out[2 * nc] = C[1] * ih;
-    out[3 * nc] = C[2] * ih;
+  }
+  // polynomial in physical offsets d = x - centroid:
+  //   Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
+  const R ih = R(1) / hcell[i], ih2 = ih * ih;
+  R* out = poly + (int64_t)kPolyStride * i;
 #pragma unroll
-    for (int n = 3; n < 9; ++n) out[(n + 1) * nc] = C[n] * ih2;
+  for (int v = 0; v < 5; ++v) {
+    R C[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) C[n] = ca[v] * a[n][v];
+    C[0] += cl[0][v];
+    C[1] += cl[1][v];
+    C[2] += cl[2][v];
+    const R shift = C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] + C[7] * m2[4] +
+                    C[8] * m2[5];
+    R* o = out + 10 * v;
+    o[0] = c0.value_minus(v, shift);
+    o[1] = C[0] * ih;
+    o[2] = C[1] * ih;
+    o[3] = C[2] * ih;
+#pragma unroll
+    for (int n = 3; n < 9; ++n) o[n + 1] = C[n] * ih2;
   }
 }
 
-// Coefficient accessor of one cell's polynomial in the SoA array [50][nc].
+// Coefficient accessor of one cell's polynomial (kPolyStride values per cell).
 template <class R>
 struct PolyRef {
   const R* __restrict__ p;
-  int64_t nc, c;
-  __device__ __forceinline__ R operator()(int v, int j) const { return p[(int64_t)(10 * v + j) * nc + c]; }
+  __device__ __forceinline__ R operator()(int v, int j) const { return __ldg(p + 10 * v + j); }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -169,9 +331,9 @@ __global__ void __launch_bounds__(128) k_flux(
     }
     const R w = fgp[9 * stride + gid];
     R vl[5], gl[5][3], vr[5], gr[5][3];
-    eval_poly(PolyRef<R>{poly, nc, o}, dl, vl, gl);
+    eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * o}, dl, vl, gl);
     if (nb >= 0) {
-      eval_poly(PolyRef<R>{poly, nc, nb}, dr, vr, gr);
+      eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
     } else {
       // mirror image of the owner across the wall plane (axis `wall`)
 #pragma unroll
@@ -197,10 +359,12 @@ __global__ void __launch_bounds__(128) k_flux(
       for (int v = 0; v < 5; ++v)
         if (v != 1 + wall) acc[v] = acc[5 + v] = R(0);
     }
+    R* o = fface + (int64_t)kFaceStride * f;
 #pragma unroll
-    for (int q = 0; q < 10; ++q) fface[q * nf + f] = acc[q];
+    for (int q = 0; q < 10; ++q) o[q] = acc[q];
   }
 }
+
 
 template <class R>
 __device__ __forceinline__ bool physical(const double q[5], double gamma) {
@@ -210,24 +374,24 @@ __device__ __forceinline__ bool physical(const double q[5], double gamma) {
 }
 
 // Per cell: L = -(1/|Omega|) sum_f s_f F_f in the cell's fixed face order (FP64), then the
-// requested update.
+// requested update; the stage kernels also write the gather copy of the state they produce.
 template <class R>
 __global__ void __launch_bounds__(256) k_gather(
-    int64_t nc, int64_t nf, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
     const R* __restrict__ fface, const double* __restrict__ vol, int mode, double dt, double gamma,
     double* __restrict__ L, double* __restrict__ Lt, double* __restrict__ Qn,
-    double* __restrict__ Qs, int* flag) {
+    double* __restrict__ Qs, R* __restrict__ QA, R* __restrict__ QsA, int* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   double s[10];
 #pragma unroll
   for (int q = 0; q < 10; ++q) s[q] = 0.0;
   for (int k = cf_ptr[i]; k < cf_ptr[i + 1]; ++k) {
-    const int32_t e = cf_idx[k];
-    const int64_t f = e >> 1;
-    const double sg = (e & 1) ? 1.0 : -1.0;  // owner loses the outward flux
+    const int32_t e = __ldg(cf_idx + k);
+    const R* fp = fface + (int64_t)kFaceStride * (e >> 1);
+    const double sg = (e & 1) ? 1.0 : -1.0;  // the owner loses the outward flux
 #pragma unroll
-    for (int q = 0; q < 10; ++q) s[q] += sg * (double)fface[q * nf + f];
+    for (int q = 0; q < 10; ++q) s[q] += sg * (double)__ldg(fp + q);
   }
   const double iv = 1.0 / vol[i];
   double l[5], lt[5];
@@ -253,6 +417,7 @@ __global__ void __launch_bounds__(256) k_gather(
       q[v] = Qn[v * nc + i] + 0.5 * dt * l[v] + (dt * dt / 8.0) * lt[v];
       Qs[v * nc + i] = q[v];
     }
+    Gq<R>::store(QsA, i, q);
   } else {
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -260,17 +425,24 @@ __global__ void __launch_bounds__(256) k_gather(
              (dt * dt / 6.0) * (Lt[v * nc + i] + 2.0 * lt[v]);
       Qn[v * nc + i] = q[v];
     }
+    Gq<R>::store(QA, i, q);
   }
   if (!physical<R>(q, gamma)) atomicOr(flag, kErrNonphysical);
 }
 
+template <class R>
 __global__ void k_permute_in(int64_t nc, const int32_t* __restrict__ perm,
-                             const double* __restrict__ src, double* __restrict__ dst) {
+                             const double* __restrict__ src, double* __restrict__ dst, R* gq) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   const int64_t c = perm[i];
+  double q[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) dst[v * nc + i] = src[v * nc + c];
+  for (int v = 0; v < 5; ++v) {
+    q[v] = src[v * nc + c];
+    dst[v * nc + i] = q[v];
+  }
+  if (gq) Gq<R>::store(gq, i, q);
 }
 __global__ void k_permute_out(int64_t nc, const int32_t* __restrict__ perm,
                               const double* __restrict__ src, double* __restrict__ dst) {
@@ -334,10 +506,10 @@ __global__ void k_dt_final(const double* partial, int n, double* out) {
 }  // namespace
 
 template <class R>
-void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const double* Q,
+void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                   R* poly, cudaStream_t st) {
-  k_recon<R><<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, Q, m.st_ptr, m.st_idx, m.st_sub,
-                                                      m.n_sub, m.sb_ptr, g.Ap, g.Bp, g.mom, g.h,
+  k_recon<R><<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, QA, m.st_ptr, m.st_idx, m.n_sub,
+                                                      m.sb_ptr, m.sub_cnt, g.Ap, g.Bp, g.mom, g.h,
                                                       p.weno_gamma, p.weno_eps, p.weno_pow, poly);
 }
 template <class R>
@@ -356,14 +528,15 @@ void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const 
 }
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
-                   double gamma, double* L, double* Lt, double* Qn, double* Qs, int* flag,
-                   cudaStream_t st) {
-  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.nf, m.cf_ptr, m.cf_idx, fface, g.vol,
-                                                       mode, dt, gamma, L, Lt, Qn, Qs, flag);
+                   double gamma, double* L, double* Lt, double* Qn, double* Qs, R* QA, R* QsA,
+                   int* flag, cudaStream_t st) {
+  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.vol, mode,
+                                                       dt, gamma, L, Lt, Qn, Qs, QA, QsA, flag);
 }
-void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst,
+template <class R>
+void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst, R* gq,
                        cudaStream_t st) {
-  k_permute_in<<<blocks_for(nc, 256), 256, 0, st>>>(nc, perm, src, dst);
+  k_permute_in<R><<<blocks_for(nc, 256), 256, 0, st>>>(nc, perm, src, dst, gq);
 }
 void launch_permute_out(int64_t nc, const int32_t* perm, const double* src, double* dst,
                         cudaStream_t st) {
@@ -384,15 +557,21 @@ void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, dou
 
 template void launch_recon<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
                                    const double*, double*, cudaStream_t);
+template void launch_permute_in<double>(int64_t, const int32_t*, const double*, double*, double*,
+                                        cudaStream_t);
+template void launch_permute_in<float>(int64_t, const int32_t*, const double*, double*, float*,
+                                       cudaStream_t);
 template void launch_recon<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
-                                  const double*, float*, cudaStream_t);
+                                  const float*, float*, cudaStream_t);
 template void launch_flux<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
                                   const double*, double, double*, int*, cudaStream_t);
 template void launch_flux<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
                                  const float*, double, float*, int*, cudaStream_t);
 template void launch_gather<double>(const DevMesh&, const Geo64&, const double*, int, double, double,
-                                    double*, double*, double*, double*, int*, cudaStream_t);
+                                    double*, double*, double*, double*, double*, double*, int*,
+                                    cudaStream_t);
 template void launch_gather<float>(const DevMesh&, const Geo64&, const float*, int, double, double,
-                                   double*, double*, double*, double*, int*, cudaStream_t);
+                                   double*, double*, double*, double*, float*, float*, int*,
+                                   cudaStream_t);
 
 }  // namespace gks

@@ -45,6 +45,7 @@ struct HostMesh {
   std::vector<uint8_t> st_sub;          // bit m set if the member is in sub-stencil m
   std::vector<int8_t> n_sub;            // M per cell
   std::vector<int32_t> sb_ptr;          // offset of each cell's (member, sub-stencil) pairs
+  std::vector<uint64_t> sub_cnt;        // byte s: number of members of sub-stencil s
 };
 
 struct DeviceGeom;  // defined in the CUDA sources

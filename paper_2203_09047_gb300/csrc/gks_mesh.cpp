@@ -409,6 +409,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
   m.st_ptr.assign(nc + 1, 0);
   m.n_sub.resize(nc);
   m.sb_ptr.assign(nc + 1, 0);
+  m.sub_cnt.assign(nc, 0);
   m.st_idx.clear();
   m.st_xf.clear();
   m.st_sub.clear();
@@ -481,6 +482,13 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
     }
     m.st_ptr[i + 1] = m.st_ptr[i] + (int32_t)list.size();
     m.sb_ptr[i + 1] = m.sb_ptr[i] + pairs;
+    uint64_t cnt = 0;  // members per sub-stencil, one byte each
+    for (int s = 0; s < M; ++s) {
+      uint64_t c = 0;
+      for (size_t k = 0; k < list.size(); ++k) c += (sub[k] >> s) & 1u;
+      cnt |= c << (8 * s);
+    }
+    m.sub_cnt[i] = cnt;
   }
   return GKS_OK;
 }

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #pragma nv_diag_suppress 20011
+#pragma nv_diag_suppress 20014
 #include "gks_kinetic.cuh"
 
 namespace gks {
