@@ -2,6 +2,7 @@
 // two-stage fourth-order stepping and the time-step bound.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -129,9 +130,10 @@ template <class R>
 gks_status alloc_geo(gks_solver* s, GeoR<R>& g) {
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e;
-  if ((e = salloc(s, &g.Ap, (int64_t)Lay<R>::apad * s->m.nst)) != cudaSuccess)
+  if ((e = salloc(s, &g.Ap, 9 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess)
     return s->cuda_fail(e, "alloc A+");
-  if ((e = salloc(s, &g.Bp, 4 * s->m.nsb)) != cudaSuccess) return s->cuda_fail(e, "alloc B");
+  if ((e = salloc(s, &g.Bp, 4 * (int64_t)kTile * s->m.n_tsb)) != cudaSuccess)
+    return s->cuda_fail(e, "alloc B");
   if ((e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc moments");
   if ((e = salloc(s, &g.h, nc)) != cudaSuccess) return s->cuda_fail(e, "alloc h");
   if ((e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face data");
@@ -301,6 +303,7 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   m.nf = h.n_faces;
   m.nst = (int64_t)h.st_idx.size();
   m.nsb = h.sb_ptr.back();
+  for (int64_t i = 0; i < h.n_cells; ++i) m.kmax = std::max(m.kmax, h.st_ptr[i + 1] - h.st_ptr[i]);
   cudaError_t e = cudaSuccess;
   auto bad = [&](const char* what) {
     gks_status r = e == cudaErrorMemoryAllocation ? GKS_E_NOMEM : GKS_E_CUDA;
@@ -325,6 +328,14 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.n_sub, h.n_sub)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.sb_ptr, h.sb_ptr)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.sub_cnt, h.sub_cnt)) != cudaSuccess) return bad("upload");
+  m.n_tiles = h.n_tiles;
+  m.n_tslots = h.t_st.back();
+  m.n_tsb = h.t_sb.back();
+  if ((e = supload(s, &m.t_K, h.t_K)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.t_cnt, h.t_cnt)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.t_st, h.t_st)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.t_sb, h.t_sb)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &m.t_idx, h.t_idx)) != cudaSuccess) return bad("upload");
   const int64_t nc = m.nc, nf = m.nf;
   if ((e = salloc(s, &s->g.vol, nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.cen, 3 * nc)) != cudaSuccess) return bad("alloc");
@@ -460,15 +471,15 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
 
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
   if (!s || !bytes) return GKS_E_INVAL;
-  const double nc = (double)s->m.nc, nf = (double)s->m.nf, nst = (double)s->m.nst,
-               nsb = (double)s->m.nsb, ncf = 2.0 * nf;  // each face appears in two cells
+  const double nc = (double)s->m.nc, nf = (double)s->m.nf;
+  const double ncf = 2.0 * nf;  // each face appears in two cells
   const double r = s->mixed ? 4.0 : 8.0;
-  const double ap = s->mixed ? Lay<float>::apad : Lay<double>::apad;
-  // reconstruction: gather copy of Q (48 B per cell, own + stencil, once), CSR offsets and
-  // counts, stencil entries, pseudo-inverse rows, sub-stencil entries, cell moments and size,
-  // polynomial coefficients written
-  bytes[0] = 48.0 * nc + 4.0 * (nc + 1) + nc + 4.0 * (nc + 1) + 8.0 * nc + 4.0 * nst +
-             ap * r * nst + 4.0 * r * nsb + 7.0 * r * nc + kPolyStride * r * nc;
+  const double ts = (double)kTile * s->m.n_tslots, tb = (double)kTile * s->m.n_tsb;
+  // reconstruction: gather copy of Q (48 B per cell, own + stencil, once), tile counts and
+  // offsets, interleaved stencil entries, pseudo-inverse rows and sub-stencil entries (with the
+  // tile padding, 0.4 % on the hybrid mesh), cell moments and size, polynomial written
+  bytes[0] = 48.0 * nc + 24.0 * (double)s->m.n_tiles + nc + 4.0 * ts + 9.0 * r * ts +
+             4.0 * r * tb + 7.0 * r * nc + kPolyStride * r * nc;
   // flux: face cells and wall flag, Gauss data, polynomials read, face fluxes written
   bytes[1] = 9.0 * nf + 40.0 * r * nf + kPolyStride * r * nc + kFaceStride * r * nf;
   // face sums + stage update: CSR, face fluxes, volumes, Q^n read, L/Lt and the stage state,

@@ -13,9 +13,10 @@ namespace gks {
 // Storage layouts of the hot path.
 //  - gather copy of the state, 48 bytes per cell: FP32 path [hi0..hi4, lo0..lo4, 0, 0] with
 //    hi = (float)q and lo = (float)(q - hi); FP64 path [q0..q4, 0];
-//  - pseudo-inverse rows: one row of Lay<R>::apad values per stencil member (9 used);
-//  - sub-stencil entries: 4 values {B_0k, B_1k, B_2k, k} per (sub-stencil, member), sub-stencil
-//    major within a cell;
+//  - tiles of 32 consecutive cells; within a tile every per-member array is interleaved over the
+//    32 lanes: stencil entries [t_st[t] + k][32], pseudo-inverse rows [(t_st[t] + k) 9 + n][32],
+//    sub-stencil entries {B_0, B_1, B_2, member index} [(t_sb[t] + slot) 4 + c][32], padded to
+//    the tile's largest stencil and per-sub-stencil counts (padding contributes zero);
 //  - cell polynomials: kPolyStride values per cell, variable v at offset 10 v;
 //  - face fluxes: kFaceStride values per face (F^n 0..4, dF/dt 5..9).
 template <class R>
@@ -42,6 +43,7 @@ enum : int {
 // Mesh arrays on the device (internal order).
 struct DevMesh {
   int64_t nc = 0, nf = 0, nst = 0, nsb = 0;
+  int kmax = 0;  // largest big stencil
   int32_t* perm = nullptr;
   int8_t* type = nullptr;
   double* cell_x = nullptr;   // [nc][24]
@@ -59,6 +61,12 @@ struct DevMesh {
   int8_t* n_sub = nullptr;
   int32_t* sb_ptr = nullptr;
   uint64_t* sub_cnt = nullptr;
+  int64_t n_tiles = 0, n_tslots = 0, n_tsb = 0;
+  int32_t* t_K = nullptr;
+  uint64_t* t_cnt = nullptr;
+  int32_t* t_st = nullptr;
+  int32_t* t_sb = nullptr;
+  int32_t* t_idx = nullptr;
 };
 
 // FP64 geometry (always kept).
@@ -74,8 +82,8 @@ struct Geo64 {
 // Geometry in the arithmetic precision R of the hot path.
 template <class R>
 struct GeoR {
-  R* Ap = nullptr;   // per stencil member a row of Lay<R>::apad values (9 used)
-  R* Bp = nullptr;   // per (sub-stencil, member) pair: {3 coefficients, member index}
+  R* Ap = nullptr;   // pseudo-inverse rows, tile-interleaved
+  R* Bp = nullptr;   // sub-stencil entries, tile-interleaved
   R* mom = nullptr;  // [6][nc]
   R* h = nullptr;    // [nc]
   R* fgp = nullptr;  // [10][4 nf]: dl(3) dr(3) n1(3) w, index 4 f + gauss point

@@ -192,7 +192,8 @@ template <class R>
 __global__ void __launch_bounds__(kThreads) k_geom_ls(
     int64_t nc, const int32_t* __restrict__ st_ptr, const int32_t* __restrict__ st_idx,
     const double* __restrict__ st_xf, const uint8_t* __restrict__ st_sub,
-    const int8_t* __restrict__ n_sub, const int32_t* __restrict__ sb_ptr,
+    const int8_t* __restrict__ n_sub, const int32_t* __restrict__ t_st,
+    const int32_t* __restrict__ t_sb, const uint64_t* __restrict__ t_cnt,
     const double* __restrict__ cen, const double* __restrict__ hh, const double* __restrict__ mom,
     R* Ap, R* Bp, int* flag, int* bad_cell) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -222,10 +223,13 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
       A[k + (3 + q) * K] = d[pa[q]] * d[pb[q]] + mj * r2 - m0[q];
     }
   }
-  // sub-stencils first (they only need the linear columns); entries sub-stencil major
+  // sub-stencils first (they only need the linear columns); entries sub-stencil major in the
+  // tile-interleaved layout
   const int M = n_sub[i];
-  const int b0 = sb_ptr[i];
-  int pos = 0;
+  const int64_t tile = i / kTile;
+  const int lane = (int)(i % kTile);
+  const uint64_t tc = t_cnt[tile];
+  int slot0 = 0;  // first slot of sub-stencil s within the tile
   for (int s = 0; s < M; ++s) {
     double S[kMaxStencil * 3];
     int idx[kMaxStencil];
@@ -243,23 +247,21 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
     for (int r = 0; r < km; ++r) {
       double out[3];
       pinv_column(S, km, 3, sb, srd, r, x, out);
-      R* e = Bp + 4 * (int64_t)(b0 + pos);
-      for (int a = 0; a < 3; ++a) e[a] = (R)out[a];
-      e[3] = (R)idx[r];  // member index, exact in either precision
-      ++pos;
+      const int64_t slot = (int64_t)t_sb[tile] + slot0 + r;
+      for (int a = 0; a < 3; ++a) Bp[(4 * slot + a) * kTile + lane] = (R)out[a];
+      Bp[(4 * slot + 3) * kTile + lane] = (R)idx[r];  // member index, exact in either precision
     }
+    slot0 += (int)((tc >> (8 * s)) & 0xffu);
   }
   if (!qr_inplace(A, K, 9, beta, rd)) {
     atomicOr(flag, kErrSingular);
     atomicMin(bad_cell, (int)i);
     return;
   }
-  constexpr int ap = Lay<R>::apad;
   for (int k = 0; k < K; ++k) {
     pinv_column(A, K, 9, beta, rd, k, x, col);
-    R* row = Ap + (int64_t)ap * (s0 + k);
-    for (int n = 0; n < 9; ++n) row[n] = (R)col[n];
-    for (int n = 9; n < ap; ++n) row[n] = R(0);
+    const int64_t row = (int64_t)t_st[tile] + k;
+    for (int n = 0; n < 9; ++n) Ap[((9 * row) + n) * kTile + lane] = (R)col[n];
   }
 }
 
@@ -292,9 +294,12 @@ void launch_geom_hdt(const DevMesh& m, const Geo64& g, cudaStream_t st) {
 template <class R>
 void launch_geom_ls(const DevMesh& m, const Geo64& g, GeoR<R>& gr, int* flag, int* bad_cell,
                     cudaStream_t st) {
+  // padding of the tile layouts must read as zero coefficients
+  cudaMemsetAsync(gr.Ap, 0, sizeof(R) * 9 * kTile * (size_t)m.n_tslots, st);
+  cudaMemsetAsync(gr.Bp, 0, sizeof(R) * 4 * kTile * (size_t)m.n_tsb, st);
   k_geom_ls<R><<<blocks_for(m.nc, 64), 64, 0, st>>>(m.nc, m.st_ptr, m.st_idx, m.st_xf, m.st_sub,
-                                                      m.n_sub, m.sb_ptr, g.cen, g.h, g.mom, gr.Ap,
-                                                      gr.Bp, flag, bad_cell);
+                                                      m.n_sub, m.t_st, m.t_sb, m.t_cnt, g.cen, g.h,
+                                                      g.mom, gr.Ap, gr.Bp, flag, bad_cell);
 }
 template <class R>
 void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st) {

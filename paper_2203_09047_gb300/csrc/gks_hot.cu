@@ -83,42 +83,6 @@ __device__ __forceinline__ void stencil_delta(const R* __restrict__ QA, int32_t 
   for (int v = 0; v < 5; ++v) dq[v] = g.minus(c0, v);
 }
 
-template <class R>
-__device__ __forceinline__ void load_row9(const R* __restrict__ p, R r[9]);
-template <>
-__device__ __forceinline__ void load_row9<float>(const float* __restrict__ p, float r[9]) {
-  const float4* q = reinterpret_cast<const float4*>(p);
-  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
-  r[8] = c.x;
-}
-template <>
-__device__ __forceinline__ void load_row9<double>(const double* __restrict__ p, double r[9]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double2 a = __ldg(q + k);
-    r[2 * k] = a.x;
-    r[2 * k + 1] = a.y;
-  }
-  r[8] = __ldg(p + 8);
-}
-template <class R>
-__device__ __forceinline__ void load_entry(const R* __restrict__ p, R e[3], int& k);
-template <>
-__device__ __forceinline__ void load_entry<float>(const float* __restrict__ p, float e[3], int& k) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-  e[0] = a.x; e[1] = a.y; e[2] = a.z;
-  k = (int)a.w;
-}
-template <>
-__device__ __forceinline__ void load_entry<double>(const double* __restrict__ p, double e[3], int& k) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  e[0] = a.x; e[1] = a.y; e[2] = b.x;
-  k = (int)b.y;
-}
-
 // ------------------------------------------------------------------------------------------
 // Reconstruction: one thread per cell, all five conserved variables at once.
 //   pass 1 over the big stencil:  a   = A+ dq           (quadratic P0, 9 coefficients per variable
@@ -128,24 +92,41 @@ __device__ __forceinline__ void load_entry<double>(const double* __restrict__ p,
 //     C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m,
 //   pass 3 over the sub-stencils accumulates sum_m (...) b_m without storing the b_m.
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
+constexpr int kReconThreads = 64;
+
 template <class R>
-__global__ void __launch_bounds__(128) k_recon(
-    int64_t nc, const R* __restrict__ QA, const int32_t* __restrict__ st_ptr,
-    const int32_t* __restrict__ st_idx, const int8_t* __restrict__ n_sub,
-    const int32_t* __restrict__ sb_ptr, const uint64_t* __restrict__ sub_cnt,
-    const R* __restrict__ Ap, const R* __restrict__ Bp, const R* __restrict__ mom,
-    const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly) {
+__global__ void __launch_bounds__(kReconThreads) k_recon(
+    int64_t nc, const R* __restrict__ QA, const int32_t* __restrict__ t_K,
+    const uint64_t* __restrict__ t_cnt, const int32_t* __restrict__ t_st,
+    const int32_t* __restrict__ t_sb, const int32_t* __restrict__ t_idx,
+    const int8_t* __restrict__ n_sub, const R* __restrict__ Ap, const R* __restrict__ Bp,
+    const R* __restrict__ mom, const R* __restrict__ hcell, R wg, R weps, int wpow,
+    R* __restrict__ poly) {
+  // stencil differences of this thread's cell, [member][variable][thread] (conflict-free)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sdq = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
-  constexpr int ap = Lay<R>::apad;
-  const int s0 = st_ptr[i];
-  const int K = st_ptr[i + 1] - s0;
+  // tile-interleaved stencil data: every load below is one 128-byte line per warp, and the
+  // loop bounds are the tile's (uniform across the warp)
+  const int64_t tile = i / kTile;
+  const int lane = (int)(i % kTile);
+  const int K = __ldg(t_K + tile);
+  const uint64_t cnt = __ldg(t_cnt + tile);
   const int M = n_sub[i];
-  const uint64_t cnt = sub_cnt[i];
-  const R* Bc = Bp + 4 * (int64_t)sb_ptr[i];
-  const int32_t* sidx = st_idx + s0;
+  const int32_t* sidx = t_idx + (int64_t)__ldg(t_st + tile) * kTile + lane;
+  const R* A = Ap + (int64_t)__ldg(t_st + tile) * 9 * kTile + lane;
+  const R* Bt = Bp + (int64_t)__ldg(t_sb + tile) * 4 * kTile + lane;
   Gq<R> c0;
   c0.load(QA, i);
+  // gather: every stencil difference once, independent iterations (many loads in flight)
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    R dq[5];
+    stencil_delta(QA, __ldg(sidx + k * kTile), c0, dq);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kReconThreads] = dq[v];
+  }
   // pass 1: big-stencil least squares
   R a[9][5];
 #pragma unroll
@@ -154,8 +135,10 @@ __global__ void __launch_bounds__(128) k_recon(
     for (int v = 0; v < 5; ++v) a[n][v] = R(0);
   for (int k = 0; k < K; ++k) {
     R dq[5], row[9];
-    stencil_delta(QA, __ldg(sidx + k), c0, dq);
-    load_row9(Ap + (int64_t)ap * (s0 + k), row);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) row[n] = __ldg(A + (9 * k + n) * kTile);
 #pragma unroll
     for (int n = 0; n < 9; ++n)
 #pragma unroll
@@ -183,23 +166,26 @@ __global__ void __launch_bounds__(128) k_recon(
   // pass 2: sub-stencil fits and their indicators
   R bet[kMaxSub][5];
   {
-    const R* e = Bc;
+    const R* e = Bt;
 #pragma unroll
     for (int s = 0; s < kMaxSub; ++s) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) bet[s][v] = R(0);
-      if (s < M) {
+      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+      if (cs > 0) {
         R b[3][5];
 #pragma unroll
         for (int t = 0; t < 3; ++t)
 #pragma unroll
           for (int v = 0; v < 5; ++v) b[t][v] = R(0);
-        const int cs = (int)((cnt >> (8 * s)) & 0xffu);
-        for (int j = 0; j < cs; ++j, e += 4) {
+        for (int j = 0; j < cs; ++j, e += 4 * kTile) {
           R coef[3], dq[5];
-          int k;
-          load_entry(e, coef, k);
-          stencil_delta(QA, __ldg(sidx + k), c0, dq);
+          const int k = (int)__ldg(e + 3 * kTile);
+          coef[0] = __ldg(e);
+          coef[1] = __ldg(e + kTile);
+          coef[2] = __ldg(e + 2 * kTile);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
 #pragma unroll
           for (int t = 0; t < 3; ++t)
 #pragma unroll
@@ -240,8 +226,7 @@ __global__ void __launch_bounds__(128) k_recon(
     ca[v] = wb0 / g0;
     const R corr = wb0 * wg / g0;
 #pragma unroll
-    for (int s = 0; s < kMaxSub; ++s)
-      if (s < M) bet[s][v] = bet[s][v] * is - corr;
+    for (int s = 0; s < kMaxSub; ++s) bet[s][v] = s < M ? bet[s][v] * is - corr : R(0);
   }
   // pass 3: linear part of the combination, sum_m cs_m b_m
   R cl[3][5];
@@ -250,16 +235,19 @@ __global__ void __launch_bounds__(128) k_recon(
 #pragma unroll
     for (int v = 0; v < 5; ++v) cl[t][v] = R(0);
   {
-    const R* e = Bc;
+    const R* e = Bt;
 #pragma unroll
     for (int s = 0; s < kMaxSub; ++s) {
-      if (s < M) {
-        const int cs = (int)((cnt >> (8 * s)) & 0xffu);
-        for (int j = 0; j < cs; ++j, e += 4) {
+      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+      {
+        for (int j = 0; j < cs; ++j, e += 4 * kTile) {
           R coef[3], dq[5];
-          int k;
-          load_entry(e, coef, k);
-          stencil_delta(QA, __ldg(sidx + k), c0, dq);
+          const int k = (int)__ldg(e + 3 * kTile);
+          coef[0] = __ldg(e);
+          coef[1] = __ldg(e + kTile);
+          coef[2] = __ldg(e + 2 * kTile);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             const R w = bet[s][v] * dq[v];
@@ -373,7 +361,53 @@ __device__ __forceinline__ bool physical(const double q[5], double gamma) {
   return q[0] > 0.0 && p > 0.0;
 }
 
-// Per cell: L = -(1/|Omega|) sum_f s_f F_f in the cell's fixed face order (FP64), then the
+// Sum of the signed face fluxes of one cell (the owner loses the outward flux), in the cell's
+// fixed face order. FP64 path: FP64 sums. FP32 path: each component is accumulated as an
+// unevaluated pair hi + lo of floats with the error-free TwoSum (Knuth), so the sum is exact to
+// about 2^-48 relative without FP64 arithmetic (GB300 runs FP64 at 1/64 of the FP32 rate).
+template <class R>
+__device__ __forceinline__ void face_sums(int k0, int k1, const int32_t* __restrict__ cf_idx,
+                                          const R* __restrict__ fface, double s[10]);
+template <>
+__device__ __forceinline__ void face_sums<double>(int k0, int k1, const int32_t* __restrict__ cf_idx,
+                                                  const double* __restrict__ fface, double s[10]) {
+#pragma unroll
+  for (int q = 0; q < 10; ++q) s[q] = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const int32_t e = __ldg(cf_idx + k);
+    const double* fp = fface + (int64_t)kFaceStride * (e >> 1);
+    const double sg = (e & 1) ? 1.0 : -1.0;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) s[q] += sg * __ldg(fp + q);
+  }
+}
+template <>
+__device__ __forceinline__ void face_sums<float>(int k0, int k1, const int32_t* __restrict__ cf_idx,
+                                                 const float* __restrict__ fface, double s[10]) {
+  float hi[10], lo[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) hi[q] = lo[q] = 0.f;
+  for (int k = k0; k < k1; ++k) {
+    const int32_t e = __ldg(cf_idx + k);
+    const float4* fp = reinterpret_cast<const float4*>(fface + (int64_t)kFaceStride * (e >> 1));
+    const float4 a = __ldg(fp), b = __ldg(fp + 1), c = __ldg(fp + 2);
+    float x[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+    const bool neg = !(e & 1);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      const float xv = neg ? -x[q] : x[q];
+      const float t = __fadd_rn(hi[q], xv);
+      const float bb = __fsub_rn(t, hi[q]);
+      const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(t, bb)), __fsub_rn(xv, bb));
+      hi[q] = t;
+      lo[q] = __fadd_rn(lo[q], err);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 10; ++q) s[q] = (double)hi[q] + (double)lo[q];
+}
+
+// Per cell: L = -(1/|Omega|) sum_f s_f F_f in the cell's fixed face order, then the
 // requested update; the stage kernels also write the gather copy of the state they produce.
 template <class R>
 __global__ void __launch_bounds__(256) k_gather(
@@ -384,15 +418,7 @@ __global__ void __launch_bounds__(256) k_gather(
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   double s[10];
-#pragma unroll
-  for (int q = 0; q < 10; ++q) s[q] = 0.0;
-  for (int k = cf_ptr[i]; k < cf_ptr[i + 1]; ++k) {
-    const int32_t e = __ldg(cf_idx + k);
-    const R* fp = fface + (int64_t)kFaceStride * (e >> 1);
-    const double sg = (e & 1) ? 1.0 : -1.0;  // the owner loses the outward flux
-#pragma unroll
-    for (int q = 0; q < 10; ++q) s[q] += sg * (double)__ldg(fp + q);
-  }
+  face_sums(cf_ptr[i], cf_ptr[i + 1], cf_idx, fface, s);
   const double iv = 1.0 / vol[i];
   double l[5], lt[5];
 #pragma unroll
@@ -508,9 +534,12 @@ __global__ void k_dt_final(const double* partial, int n, double* out) {
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                   R* poly, cudaStream_t st) {
-  k_recon<R><<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, QA, m.st_ptr, m.st_idx, m.n_sub,
-                                                      m.sb_ptr, m.sub_cnt, g.Ap, g.Bp, g.mom, g.h,
-                                                      p.weno_gamma, p.weno_eps, p.weno_pow, poly);
+  const size_t smem = (size_t)m.kmax * 5 * kReconThreads * sizeof(R);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_recon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_recon<R><<<blocks_for(m.nc, kReconThreads), kReconThreads, smem, st>>>(
+      m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb, m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h,
+      p.weno_gamma, p.weno_eps, p.weno_pow, poly);
 }
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,

@@ -16,6 +16,7 @@ constexpr int kFlipShift = 28;
 constexpr int32_t kCellMask = (1 << kFlipShift) - 1;
 constexpr int kMaxStencil = 64;  // largest big stencil accepted
 constexpr int kMaxSub = 8;       // largest number of sub-stencils (hexahedra, pyramids)
+constexpr int kTile = 32;        // cells per tile of the interleaved stencil layouts
 
 // Affine per-axis map x' = s x + t between cell frames (periodic shift or mirror image).
 struct Xf {
@@ -46,6 +47,12 @@ struct HostMesh {
   std::vector<int8_t> n_sub;            // M per cell
   std::vector<int32_t> sb_ptr;          // offset of each cell's (member, sub-stencil) pairs
   std::vector<uint64_t> sub_cnt;        // byte s: number of members of sub-stencil s
+  // 32-cell tiles (cells 32 t .. 32 t + 31)
+  int64_t n_tiles = 0;
+  std::vector<int32_t> t_K;             // largest stencil of the tile
+  std::vector<uint64_t> t_cnt;          // byte s: largest member count of sub-stencil s
+  std::vector<int32_t> t_st, t_sb;      // prefix sums of t_K and of the t_cnt bytes
+  std::vector<int32_t> t_idx;           // [t_st[nt]][32] interleaved stencil entries
 };
 
 struct DeviceGeom;  // defined in the CUDA sources

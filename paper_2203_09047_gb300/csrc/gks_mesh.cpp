@@ -6,6 +6,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gks_internal.h"
@@ -301,10 +302,11 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
     i = e;
   }
 
-  // 3. Morton order of cells by vertex mean
+  // 3. cell order: by cell kind, then Morton order of the vertex mean, so that 32-cell tiles
+  //    hold cells with (nearly) the same stencil sizes
   std::vector<int32_t> perm(nc), inv(nc);
   {
-    std::vector<std::pair<uint64_t, int32_t>> code(nc);
+    std::vector<std::tuple<int, uint64_t, int32_t>> code(nc);
     for (int64_t c = 0; c < nc; ++c) {
       double x[3] = {0, 0, 0};
       for (int s = 0; s < 8; ++s)
@@ -315,12 +317,12 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
         u = std::min(std::max(u, 0.0), 1.0);
         k |= spread21((uint64_t)(u * 2097151.0)) << a;
       }
-      code[c] = {k, (int32_t)c};
+      code[c] = std::make_tuple((int)cell_type[c], k, (int32_t)c);
     }
     std::sort(code.begin(), code.end());
     for (int64_t i = 0; i < nc; ++i) {
-      perm[i] = code[i].second;
-      inv[code[i].second] = (int32_t)i;
+      perm[i] = std::get<2>(code[i]);
+      inv[perm[i]] = (int32_t)i;
     }
   }
 
@@ -490,6 +492,42 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
     }
     m.sub_cnt[i] = cnt;
   }
+  // 7. 32-cell tiles: stencil entries interleaved across the tile's lanes, padded to the tile's
+  //    largest stencil (padding points at the cell itself, whose difference is zero) and the
+  //    tile's largest member count per sub-stencil
+  const int64_t nt = (nc + kTile - 1) / kTile;
+  m.n_tiles = nt;
+  m.t_K.assign(nt, 0);
+  m.t_cnt.assign(nt, 0);
+  m.t_st.assign(nt + 1, 0);
+  m.t_sb.assign(nt + 1, 0);
+  for (int64_t t = 0; t < nt; ++t) {
+    int K = 0;
+    int cmax[kMaxSub] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t c = t * kTile; c < std::min<int64_t>(nc, (t + 1) * kTile); ++c) {
+      K = std::max(K, m.st_ptr[c + 1] - m.st_ptr[c]);
+      for (int q = 0; q < kMaxSub; ++q) cmax[q] = std::max(cmax[q], (int)((m.sub_cnt[c] >> (8 * q)) & 0xff));
+    }
+    uint64_t cw = 0;
+    int tot = 0;
+    for (int q = 0; q < kMaxSub; ++q) {
+      cw |= (uint64_t)cmax[q] << (8 * q);
+      tot += cmax[q];
+    }
+    m.t_K[t] = K;
+    m.t_cnt[t] = cw;
+    m.t_st[t + 1] = m.t_st[t] + K;
+    m.t_sb[t + 1] = m.t_sb[t] + tot;
+  }
+  m.t_idx.assign((size_t)m.t_st[nt] * kTile, 0);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int l = 0; l < kTile; ++l) {
+      const int64_t c = t * kTile + l;
+      const int Kc = c < nc ? m.st_ptr[c + 1] - m.st_ptr[c] : 0;
+      for (int k = 0; k < m.t_K[t]; ++k)
+        m.t_idx[((size_t)m.t_st[t] + k) * kTile + l] =
+            k < Kc ? m.st_idx[m.st_ptr[c] + k] : (int32_t)(c < nc ? c : t * kTile);
+    }
   return GKS_OK;
 }
 
