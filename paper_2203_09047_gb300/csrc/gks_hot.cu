@@ -295,7 +295,7 @@ struct PolyRef {
 // the axis least aligned with n1, n3 = n1 x n2), computes F^n and dF/dt, rotates back and
 // weights by the quadrature weight; the four are summed with shuffles and written once.
 template <class R>
-__global__ void __launch_bounds__(128) k_flux(
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fgp, const R* __restrict__ poly,
     FluxParams<R> P, R dt, R* __restrict__ fface, int* flag) {

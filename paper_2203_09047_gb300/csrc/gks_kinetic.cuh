@@ -225,8 +225,13 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   // equilibrium flux moments
   R e0[5], e1[5], e2[5];
   G(M0, 1, 0, 0, 0, e0);
-  Gadotu(M0, ab, 1, e1);
   Ga(M0, Ab, 1, 0, 0, e2);
+  if (P.tau_model != 0) {
+    Gadotu(M0, ab, 1, e1);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) e1[q] = R(0);  // multiplied by tau = 0 in both flux forms
+  }
   if (!P.full) {
     // F(delta) = rho0 [delta e0 - tau delta (e1 + e2) + delta^2/2 e2]: the fit is exact.
 #pragma unroll
