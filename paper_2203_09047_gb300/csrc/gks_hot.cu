@@ -84,15 +84,27 @@ __device__ __forceinline__ void stencil_delta(const R* __restrict__ QA, int32_t 
 }
 
 // ------------------------------------------------------------------------------------------
-// Reconstruction: one thread per cell, all five conserved variables at once.
-//   pass 1 over the big stencil:  a   = A+ dq           (quadratic P0, 9 coefficients per variable
-//                                                        in centred scaled coordinates)
-//   pass 2 over the sub-stencils: b_m = B_m dq|S_m      -> beta_m (Eq. indicator)
-//   weights (Section 2): tau, omega, omega-bar; the combination of Eq. weno as one polynomial
-//     C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m,
-//   pass 3 over the sub-stencils accumulates sum_m (...) b_m without storing the b_m.
+// Reconstruction, one block of four warps per 32-cell tile (lane = cell). For each conserved
+// variable v of each cell:
+//   dq_k = Q_k - Q_0 over the big stencil                      (phase 1, all warps, to shared)
+//   a    = A+ dq   (quadratic P0, 9 coefficients in centred scaled coordinates) and
+//   b_m  = B_m dq|S_m (linear P_m) with beta_m (Eq. indicator); rows and sub-stencils are
+//   spread over the four warps                                                       (phase 2)
+//   beta_0, tau, omega, omega-bar (Section 2), one variable per warp               (phase 3)
+//   C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m, i.e. Eq. weno as one polynomial (phase 4)
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
-constexpr int kReconThreads = 64;
+// Variables are split over the warps as warp w -> v = w, and warp 0 also takes v = 4.
+constexpr int kReconWarps = 4;
+constexpr int kReconThreads = kReconWarps * kTile;
+
+template <class R>
+struct ReconShared {
+  R a[9][5][kTile];             // big-stencil coefficients
+  R b[kMaxSub][3][5][kTile];    // sub-stencil coefficients
+  R bet[kMaxSub][5][kTile];     // beta_m, then the sub-stencil factors of the combination
+  R ca[5][kTile];               // factor of a in the combination
+  // followed by dq[K][5][kTile]
+};
 
 template <class R>
 __global__ void __launch_bounds__(kReconThreads) k_recon(
@@ -102,109 +114,105 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
     const int8_t* __restrict__ n_sub, const R* __restrict__ Ap, const R* __restrict__ Bp,
     const R* __restrict__ mom, const R* __restrict__ hcell, R wg, R weps, int wpow,
     R* __restrict__ poly) {
-  // stencil differences of this thread's cell, [member][variable][thread] (conflict-free)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sdq = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nc) return;
-  // tile-interleaved stencil data: every load below is one 128-byte line per warp, and the
-  // loop bounds are the tile's (uniform across the warp)
-  const int64_t tile = i / kTile;
-  const int lane = (int)(i % kTile);
+  ReconShared<R>& sh = *reinterpret_cast<ReconShared<R>*>(smem_raw);
+  R* sdq = reinterpret_cast<R*>(smem_raw + sizeof(ReconShared<R>));  // [k][v][lane]
+  const int64_t tile = blockIdx.x;
+  const int lane = threadIdx.x & (kTile - 1);
+  const int warp = threadIdx.x / kTile;
+  const int64_t i = tile * kTile + lane;
+  const bool valid = i < nc;
+  const int64_t ic = valid ? i : tile * kTile;  // padded lanes mirror the tile's first cell
   const int K = __ldg(t_K + tile);
   const uint64_t cnt = __ldg(t_cnt + tile);
-  const int M = n_sub[i];
   const int32_t* sidx = t_idx + (int64_t)__ldg(t_st + tile) * kTile + lane;
   const R* A = Ap + (int64_t)__ldg(t_st + tile) * 9 * kTile + lane;
   const R* Bt = Bp + (int64_t)__ldg(t_sb + tile) * 4 * kTile + lane;
   Gq<R> c0;
-  c0.load(QA, i);
-  // gather: every stencil difference once, independent iterations (many loads in flight)
-#pragma unroll 4
-  for (int k = 0; k < K; ++k) {
+  c0.load(QA, ic);
+
+  // phase 1: stencil differences, members split over the warps; the loops below are unrolled
+  // so that several iterations' loads are in flight per warp
+#pragma unroll 2
+  for (int k = warp; k < K; k += kReconWarps) {
     R dq[5];
     stencil_delta(QA, __ldg(sidx + k * kTile), c0, dq);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kReconThreads] = dq[v];
+    for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kTile + lane] = dq[v];
   }
-  // pass 1: big-stencil least squares
-  R a[9][5];
+  __syncthreads();
+
+  // phase 2, all warps: rows n = warp, warp + 4, warp + 8 of a = A+ dq, and the sub-stencil
+  // fits b_m (m = warp, warp + 4) with their indicators beta_m = |b_m|^2 (scaled coordinates)
+  for (int n = warp; n < 9; n += kReconWarps) {
+    R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+      const R row = __ldg(A + (9 * k + n) * kTile);
 #pragma unroll
-  for (int n = 0; n < 9; ++n)
+      for (int v = 0; v < 5; ++v) acc[v] += row * sdq[(5 * k + v) * kTile + lane];
+    }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) a[n][v] = R(0);
-  for (int k = 0; k < K; ++k) {
-    R dq[5], row[9];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
-#pragma unroll
-    for (int n = 0; n < 9; ++n) row[n] = __ldg(A + (9 * k + n) * kTile);
-#pragma unroll
-    for (int n = 0; n < 9; ++n)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) a[n][v] += row[n] * dq[v];
+    for (int v = 0; v < 5; ++v) sh.a[n][v][lane] = acc[v];
   }
+  {
+    int slot = 0;
+    for (int s = 0; s < warp; ++s) slot += (int)((cnt >> (8 * s)) & 0xffu);
+    for (int s = warp; s < kMaxSub; s += kReconWarps) {
+      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+      const R* e = Bt + (int64_t)4 * kTile * slot;
+      R b[3][5];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+#pragma unroll
+        for (int v = 0; v < 5; ++v) b[t][v] = R(0);
+#pragma unroll 2
+      for (int j = 0; j < cs; ++j, e += 4 * kTile) {
+        const int k = (int)__ldg(e + 3 * kTile);
+        const R c[3] = {__ldg(e), __ldg(e + kTile), __ldg(e + 2 * kTile)};
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const R dq = sdq[(5 * k + v) * kTile + lane];
+#pragma unroll
+          for (int t = 0; t < 3; ++t) b[t][v] += c[t] * dq;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        sh.bet[s][v][lane] = b[0][v] * b[0][v] + b[1][v] * b[1][v] + b[2][v] * b[2][v];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) sh.b[s][t][v][lane] = b[t][v];
+      }
+      // slots of the sub-stencils this warp skips (the other warps' ones)
+      for (int q = s; q < s + kReconWarps && q < kMaxSub; ++q) slot += (int)((cnt >> (8 * q)) & 0xffu);
+    }
+  }
+  __syncthreads();
+
+  // phase 3: nonlinear weights, one variable per warp (warp 0 also does v = 4)
+  const int M = n_sub[ic];
+  const R g0 = R(1) - wg * R(M);
   R m2[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + i];
-  // beta_0: |l| = 1 terms are cell means of the squared first derivatives (linear in the scaled
-  // coordinates y, second moments m2), |l| = 2 terms the squared second derivatives
-  R beta0[5];
+  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + ic];
+  for (int v = warp; v < 5; v += kReconWarps) {
+    R a[9];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const R gx[3] = {R(2) * a[3][v], a[6][v], a[7][v]};
-    const R gy[3] = {a[6][v], R(2) * a[4][v], a[8][v]};
-    const R gz[3] = {a[7][v], a[8][v], R(2) * a[5][v]};
+    for (int n = 0; n < 9; ++n) a[n] = sh.a[n][v][lane];
+    // |l| = 1 terms: cell means of the squared first derivatives (linear in the scaled
+    // coordinates y, second moments m2); |l| = 2 terms: squared second derivatives
+    const R gx[3] = {R(2) * a[3], a[6], a[7]};
+    const R gy[3] = {a[6], R(2) * a[4], a[8]};
+    const R gz[3] = {a[7], a[8], R(2) * a[5]};
     auto qf = [&](const R g[3]) {
       return m2[0] * g[0] * g[0] + m2[1] * g[1] * g[1] + m2[2] * g[2] * g[2] +
              R(2) * (m2[3] * g[0] * g[1] + m2[4] * g[0] * g[2] + m2[5] * g[1] * g[2]);
     };
-    beta0[v] = a[0][v] * a[0][v] + a[1][v] * a[1][v] + a[2][v] * a[2][v] + qf(gx) + qf(gy) +
-               qf(gz) + R(4) * (a[3][v] * a[3][v] + a[4][v] * a[4][v] + a[5][v] * a[5][v]) +
-               a[6][v] * a[6][v] + a[7][v] * a[7][v] + a[8][v] * a[8][v];
-  }
-  // pass 2: sub-stencil fits and their indicators
-  R bet[kMaxSub][5];
-  {
-    const R* e = Bt;
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) bet[s][v] = R(0);
-      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
-      if (cs > 0) {
-        R b[3][5];
-#pragma unroll
-        for (int t = 0; t < 3; ++t)
-#pragma unroll
-          for (int v = 0; v < 5; ++v) b[t][v] = R(0);
-        for (int j = 0; j < cs; ++j, e += 4 * kTile) {
-          R coef[3], dq[5];
-          const int k = (int)__ldg(e + 3 * kTile);
-          coef[0] = __ldg(e);
-          coef[1] = __ldg(e + kTile);
-          coef[2] = __ldg(e + 2 * kTile);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
-#pragma unroll
-          for (int t = 0; t < 3; ++t)
-#pragma unroll
-            for (int v = 0; v < 5; ++v) b[t][v] += coef[t] * dq[v];
-        }
-#pragma unroll
-        for (int v = 0; v < 5; ++v) bet[s][v] = b[0][v] * b[0][v] + b[1][v] * b[1][v] + b[2][v] * b[2][v];
-      }
-    }
-  }
-  // nonlinear weights; bet[s][v] is overwritten by the sub-stencil factor of the combination
-  const R g0 = R(1) - wg * R(M);
-  R ca[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
+    const R beta0 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + qf(gx) + qf(gy) + qf(gz) +
+                    R(4) * (a[3] * a[3] + a[4] * a[4] + a[5] * a[5]) + a[6] * a[6] + a[7] * a[7] +
+                    a[8] * a[8];
     R tau = R(0);
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s)
-      if (s < M) tau += fabs(beta0[v] - bet[s][v]);
+    for (int s = 0; s < M; ++s) tau += fabs(beta0 - sh.bet[s][v][lane]);
     tau /= R(M);
     auto weight = [&](R gam, R bb) {
       const R r = tau / (bb + weps);
@@ -212,73 +220,51 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
       for (int q = 1; q < wpow; ++q) pw *= r;
       return gam * (R(1) + pw);
     };
-    const R w0 = weight(g0, beta0[v]);
+    const R w0 = weight(g0, beta0);
     R sum = w0;
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s) {
-      if (s < M) {
-        bet[s][v] = weight(wg, bet[s][v]);
-        sum += bet[s][v];
-      }
+    for (int s = 0; s < M; ++s) {
+      const R w = weight(wg, sh.bet[s][v][lane]);
+      sh.bet[s][v][lane] = w;
+      sum += w;
     }
     const R is = R(1) / sum;
     const R wb0 = w0 * is;
-    ca[v] = wb0 / g0;
     const R corr = wb0 * wg / g0;
 #pragma unroll
-    for (int s = 0; s < kMaxSub; ++s) bet[s][v] = s < M ? bet[s][v] * is - corr : R(0);
+    for (int s = 0; s < kMaxSub; ++s)
+      sh.bet[s][v][lane] = s < M ? sh.bet[s][v][lane] * is - corr : R(0);
+    sh.ca[v][lane] = wb0 / g0;
   }
-  // pass 3: linear part of the combination, sum_m cs_m b_m
-  R cl[3][5];
+  __syncthreads();
+
+  // phase 4: linear part of the combination and the output, one variable per warp
+  const R ih = R(1) / hcell[ic], ih2 = ih * ih;
+  for (int v = warp; v < 5; v += kReconWarps) {
+    R cl[3] = {R(0), R(0), R(0)};
+    for (int s = 0; s < M; ++s) {
+      const R f = sh.bet[s][v][lane];
 #pragma unroll
-  for (int t = 0; t < 3; ++t)
-#pragma unroll
-    for (int v = 0; v < 5; ++v) cl[t][v] = R(0);
-  {
-    const R* e = Bt;
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s) {
-      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
-      {
-        for (int j = 0; j < cs; ++j, e += 4 * kTile) {
-          R coef[3], dq[5];
-          const int k = (int)__ldg(e + 3 * kTile);
-          coef[0] = __ldg(e);
-          coef[1] = __ldg(e + kTile);
-          coef[2] = __ldg(e + 2 * kTile);
-#pragma unroll
-          for (int v = 0; v < 5; ++v) dq[v] = sdq[(5 * k + v) * kReconThreads];
-#pragma unroll
-          for (int v = 0; v < 5; ++v) {
-            const R w = bet[s][v] * dq[v];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) cl[t][v] += coef[t] * w;
-          }
-        }
-      }
+      for (int t = 0; t < 3; ++t) cl[t] += f * sh.b[s][t][v][lane];
     }
-  }
-  // polynomial in physical offsets d = x - centroid:
-  //   Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
-  const R ih = R(1) / hcell[i], ih2 = ih * ih;
-  R* out = poly + (int64_t)kPolyStride * i;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
+    const R ca = sh.ca[v][lane];
     R C[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) C[n] = ca[v] * a[n][v];
-    C[0] += cl[0][v];
-    C[1] += cl[1][v];
-    C[2] += cl[2][v];
-    const R shift = C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] + C[7] * m2[4] +
-                    C[8] * m2[5];
-    R* o = out + 10 * v;
-    o[0] = c0.value_minus(v, shift);
-    o[1] = C[0] * ih;
-    o[2] = C[1] * ih;
-    o[3] = C[2] * ih;
+    for (int n = 0; n < 9; ++n) C[n] = ca * sh.a[n][v][lane];
+    C[0] += cl[0];
+    C[1] += cl[1];
+    C[2] += cl[2];
+    if (valid) {
+      // Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
+      const R shift = C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] +
+                      C[7] * m2[4] + C[8] * m2[5];
+      R* o = poly + (int64_t)kPolyStride * i + 10 * v;
+      o[0] = c0.value_minus(v, shift);
+      o[1] = C[0] * ih;
+      o[2] = C[1] * ih;
+      o[3] = C[2] * ih;
 #pragma unroll
-    for (int n = 3; n < 9; ++n) o[n + 1] = C[n] * ih2;
+      for (int n = 3; n < 9; ++n) o[n + 1] = C[n] * ih2;
+    }
   }
 }
 
@@ -313,11 +299,11 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux(
     R dl[3], dr[3], n1[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      dl[a] = fgp[a * stride + gid];
-      dr[a] = fgp[(3 + a) * stride + gid];
-      n1[a] = fgp[(6 + a) * stride + gid];
+      dl[a] = __ldcs(fgp + a * stride + gid);
+      dr[a] = __ldcs(fgp + (3 + a) * stride + gid);
+      n1[a] = __ldcs(fgp + (6 + a) * stride + gid);
     }
-    const R w = fgp[9 * stride + gid];
+    const R w = __ldcs(fgp + 9 * stride + gid);
     R vl[5], gl[5][3], vr[5], gr[5][3];
     eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * o}, dl, vl, gl);
     if (nb >= 0) {
@@ -534,10 +520,10 @@ __global__ void k_dt_final(const double* partial, int n, double* out) {
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                   R* poly, cudaStream_t st) {
-  const size_t smem = (size_t)m.kmax * 5 * kReconThreads * sizeof(R);
+  const size_t smem = sizeof(ReconShared<R>) + (size_t)m.kmax * 5 * kTile * sizeof(R);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_recon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_recon<R><<<blocks_for(m.nc, kReconThreads), kReconThreads, smem, st>>>(
+  k_recon<R><<<(unsigned)m.n_tiles, kReconThreads, smem, st>>>(
       m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb, m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h,
       p.weno_gamma, p.weno_eps, p.weno_pow, poly);
 }
