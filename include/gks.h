@@ -140,9 +140,14 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
 
 /* Vector-Jacobian product of gks_residual at Q for a fixed dt:
  *   gQ = (dL/dQ)^T gL + (dLt/dQ)^T gLt,
- * all [5][n_cells] float64 in caller order, host or device. Reverse of the reconstruction,
- * nonlinear weights and gas-kinetic flux; FP64 regardless of the solver's precision.
- * Returns GKS_E_INVAL until the adjoint kernels are present in this build. */
+ * all [5][n_cells] float64 in caller order, host or device. Hand-written reverse of the face
+ * sums, the gas-kinetic flux (Eqs. flux-1/flux-2 with the collision-time models of Section 5),
+ * the Gauss-point evaluation and the WENO reconstruction (least squares, smoothness indicators
+ * and nonlinear weights of Section 2, the derivative of |x| taken as sign(x) with +1 at 0), in
+ * FP64 regardless of the solver's precision; deterministic (per-face and per-cell writes,
+ * reverse-stencil gathers, no atomics). The first call allocates the adjoint buffers (and, for
+ * a mixed-precision solver, an FP64 copy of the geometry). Synchronises the stream; returns
+ * GKS_E_NONPHYSICAL for a non-physical state. */
 gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
                             const double* gLt, double* gQ);
 

@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_cfl_dt_noalloc.argtypes = [I64, P, P, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, P, P]
     L.gks_cfl_dt_noalloc.restype = st
+    for name in ("gks_gp_flux_host", "gks_gp_flux_vjp_host", "gks_gp_face_host"):
+        getattr(L, name).restype = ctypes.c_int
     L.gks_last_error.argtypes = [P]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_destroy.argtypes = [P]
@@ -313,3 +315,9 @@ class Solver:
         Lt = self.torch.empty_like(Q)
         gks_residual(self.h, Q, dt, L, Lt)
         return L, Lt
+
+    def residual_vjp(self, Q, dt: float, gL, gLt):
+        Q, gL, gLt = self._dev(Q), self._dev(gL), self._dev(gLt)
+        gQ = self.torch.empty_like(Q)
+        gks_residual_vjp(self.h, Q, dt, gL, gLt, gQ)
+        return gQ

@@ -59,6 +59,21 @@ struct gks_solver {
   double* h_dt = nullptr;   // pinned host scalar
   std::vector<void*> owned;
   std::string err;
+  // adjoint (allocated on the first gks_residual_vjp call)
+  bool vjp_ready = false;
+  GeoR<double> gv;             // FP64 geometry (the solver's own in FP64 mode)
+  double* vQ = nullptr;        // internal-order state [5][nc]
+  double* vQA = nullptr;       // its FP64 gather copy [nc][6]
+  double* vpoly = nullptr;     // FP64 polynomials [nc][kPolyStride]
+  double* vgL = nullptr;       // internal-order cotangents [5][nc]
+  double* vgLt = nullptr;
+  double* vgpf = nullptr;      // per face, both sides: polynomial cotangents [nf][2][kPolyStride]
+  double* vgpc = nullptr;      // per cell polynomial cotangents [nc][kPolyStride]
+  double* vgdq = nullptr;      // per stencil entry (tile layout) [slots][5][32]
+  double* vgq0 = nullptr;      // [5][nc]
+  double* vgQ = nullptr;       // [5][nc]
+  int32_t* rs_ptr = nullptr;   // reverse stencil
+  int32_t* rs_pos = nullptr;
   // optional per-kernel event timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -336,6 +351,8 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.t_st, h.t_st)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_sb, h.t_sb)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_idx, h.t_idx)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &s->rs_ptr, h.rs_ptr)) != cudaSuccess) return bad("upload");
+  if ((e = supload(s, &s->rs_pos, h.rs_pos)) != cudaSuccess) return bad("upload");
   const int64_t nc = m.nc, nf = m.nf;
   if ((e = salloc(s, &s->g.vol, nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.cen, 3 * nc)) != cudaSuccess) return bad("alloc");
@@ -460,13 +477,58 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
 
 gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
                             const double* gLt, double* gQ) {
-  if (!s) return GKS_E_INVAL;
-  (void)Q;
-  (void)dt;
-  (void)gL;
-  (void)gLt;
-  (void)gQ;
-  return s->fail(GKS_E_INVAL, "the residual VJP is not available in this build");
+  if (!s || !Q || !gL || !gLt || !gQ || !(dt > 0)) return GKS_E_INVAL;
+  const int64_t nc = s->m.nc, nf = s->m.nf;
+  cudaError_t e = cudaSuccess;
+  if (!s->vjp_ready) {
+    if (s->mixed) {
+      // FP64 geometry of its own (the FP32 path keeps only FP32 copies)
+      GeoR<double>& g = s->gv;
+      if ((e = salloc(s, &g.Ap, 9 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess ||
+          (e = salloc(s, &g.Bp, 4 * (int64_t)kTile * s->m.n_tsb)) != cudaSuccess ||
+          (e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess || (e = salloc(s, &g.h, nc)) != cudaSuccess ||
+          (e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess)
+        return s->cuda_fail(e, "vjp geometry");
+      precompute_r(s, g);
+    } else {
+      s->gv = s->gd;
+    }
+    if ((e = salloc(s, &s->vQ, 5 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vQA, 6 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vpoly, (int64_t)kPolyStride * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vgL, 5 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vgLt, 5 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vgpf, 2 * (int64_t)kPolyStride * nf)) != cudaSuccess ||
+        (e = salloc(s, &s->vgpc, (int64_t)kPolyStride * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vgdq, 5 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess ||
+        (e = salloc(s, &s->vgq0, 5 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vgQ, 5 * nc)) != cudaSuccess)
+      return s->cuda_fail(e, "vjp buffers");
+    s->vjp_ready = true;
+  }
+  const size_t bytes = sizeof(double) * 5 * nc;
+  // inputs to internal order
+  if ((e = cudaMemcpyAsync(s->tmp, Q, bytes, cudaMemcpyDefault, s->st)) != cudaSuccess)
+    return s->cuda_fail(e, "vjp copy");
+  launch_permute_in<double>(nc, s->m.perm, s->tmp, s->vQ, s->vQA, s->st);
+  launch_check_state(nc, s->vQ, s->prm.gamma, s->flag, s->st);
+  if ((e = cudaMemcpyAsync(s->tmp, gL, bytes, cudaMemcpyDefault, s->st)) != cudaSuccess)
+    return s->cuda_fail(e, "vjp copy");
+  launch_permute_in<double>(nc, s->m.perm, s->tmp, s->vgL, (double*)nullptr, s->st);
+  if ((e = cudaMemcpyAsync(s->tmp, gLt, bytes, cudaMemcpyDefault, s->st)) != cudaSuccess)
+    return s->cuda_fail(e, "vjp copy");
+  launch_permute_in<double>(nc, s->m.perm, s->tmp, s->vgLt, (double*)nullptr, s->st);
+  // forward reconstruction in FP64, then the reverse passes
+  const KParams<double> kp = kparams<double>(s->prm);
+  launch_recon<double>(s->m, s->gv, kp, s->vQA, s->vpoly, s->st);
+  launch_vjp(s->m, s->g, s->gv, kp, s->vQA, s->vpoly, s->vgL, s->vgLt, dt, s->vgpf, s->vgpc,
+             s->vgdq, s->vgq0, s->vgQ, s->rs_ptr, s->rs_pos, s->flag, s->st);
+  launch_permute_out(nc, s->m.perm, s->vgQ, s->tmp, s->st);
+  if ((e = cudaMemcpyAsync(gQ, s->tmp, bytes, cudaMemcpyDefault, s->st)) != cudaSuccess)
+    return s->cuda_fail(e, "vjp copy out");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return s->cuda_fail(e, "vjp launch");
+  return check_and_clear(s);
 }
 
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {

@@ -134,4 +134,12 @@ void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, dou
                double* partial, int nblocks, double* out, cudaStream_t st);
 int dt_blocks(int64_t nc);
 
+// ---- adjoint (gks_adjoint.cu) --------------------------------------------------------------
+// gQ = (dL/dQ)^T gL + (dLt/dQ)^T gLt on internal-order arrays; poly holds the forward
+// reconstruction of the state whose FP64 gather copy is QA.
+void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const KParams<double>& p,
+                const double* QA, const double* poly, const double* gL, const double* gLt,
+                double dt, double* gpf, double* gpc, double* gdq, double* gq0, double* gQ,
+                const int32_t* rs_ptr, const int32_t* rs_pos, int* flag, cudaStream_t st);
+
 }  // namespace gks

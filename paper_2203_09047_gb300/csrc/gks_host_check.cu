@@ -1,0 +1,84 @@
+// Host instantiations of the Gauss-point flux and its vector-Jacobian product in FP64, running
+// the same templated arithmetic as the flux kernels. They let the kinetic formulas and their
+// hand-written adjoint be checked on a CPU (against the oracle and finite differences).
+#include <cstdint>
+
+#include "gks_kinetic_adj.cuh"
+
+namespace {
+gks::FluxParams<double> params_from(const double* p) {
+  // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model}
+  gks::FluxParams<double> P;
+  P.gamma = p[0];
+  P.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
+  P.mu = p[1];
+  P.tau_eps = p[2];
+  P.tau_C = p[3];
+  P.full = (int)p[4];
+  P.tau_model = (int)p[5];
+  return P;
+}
+}  // namespace
+
+// Local-frame Gauss-point flux: Fn = F^n, Ft = dF/dt (0 on success, 1 for a non-physical state).
+extern "C" int gks_gp_flux_host(const double* p, const double* ql, const double* dql,
+                                const double* qr, const double* dqr, double dt, double* Fn,
+                                double* Ft) {
+  const gks::FluxParams<double> P = params_from(p);
+  double a[3][5], b[3][5];
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 5; ++v) {
+      a[d][v] = dql[5 * d + v];
+      b[d][v] = dqr[5 * d + v];
+    }
+  return gks::gks_gp_flux(P, ql, a, qr, b, dt, Fn, Ft) ? 0 : 1;
+}
+
+// Its vector-Jacobian product: cotangents (gFn, gFt) -> (gql, gdql[3][5], gqr, gdqr[3][5]).
+extern "C" int gks_gp_flux_vjp_host(const double* p, const double* ql, const double* dql,
+                                    const double* qr, const double* dqr, double dt,
+                                    const double* gFn, const double* gFt, double* gql,
+                                    double* gdql, double* gqr, double* gdqr) {
+  const gks::FluxParams<double> P = params_from(p);
+  double a[3][5], b[3][5], ga[3][5], gb[3][5];
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 5; ++v) {
+      a[d][v] = dql[5 * d + v];
+      b[d][v] = dqr[5 * d + v];
+      ga[d][v] = gb[d][v] = 0.0;
+    }
+  for (int v = 0; v < 5; ++v) gql[v] = gqr[v] = 0.0;
+  if (!gks::gks_gp_flux_vjp(P, ql, a, qr, b, dt, gFn, gFt, gql, ga, gqr, gb)) return 1;
+  for (int d = 0; d < 3; ++d)
+    for (int v = 0; v < 5; ++v) {
+      gdql[5 * d + v] = ga[d][v];
+      gdqr[5 * d + v] = gb[d][v];
+    }
+  return 0;
+}
+
+// Global-frame Gauss-point contribution (values, gradients [5][3], unit normal, weight) and its
+// vector-Jacobian product; gacc = nullptr runs the forward only (acc[10]).
+extern "C" int gks_gp_face_host(const double* p, const double* vl, const double* gl,
+                                const double* vr, const double* gr, const double* n1, double w,
+                                double dt, double* acc, const double* gacc, double* gvl,
+                                double* ggl, double* gvr, double* ggr) {
+  const gks::FluxParams<double> P = params_from(p);
+  double GL[5][3], GR[5][3];
+  for (int v = 0; v < 5; ++v)
+    for (int a = 0; a < 3; ++a) {
+      GL[v][a] = gl[3 * v + a];
+      GR[v][a] = gr[3 * v + a];
+    }
+  if (!gks::gp_flux_global(P, vl, GL, vr, GR, n1, w, dt, acc)) return 1;
+  if (!gacc) return 0;
+  double gGL[5][3] = {}, gGR[5][3] = {};
+  for (int v = 0; v < 5; ++v) gvl[v] = gvr[v] = 0.0;
+  if (!gks::gp_flux_global_vjp(P, vl, GL, vr, GR, n1, w, dt, gacc, gvl, gGL, gvr, gGR)) return 1;
+  for (int v = 0; v < 5; ++v)
+    for (int a = 0; a < 3; ++a) {
+      ggl[3 * v + a] = gGL[v][a];
+      ggr[3 * v + a] = gGR[v][a];
+    }
+  return 0;
+}

@@ -53,6 +53,9 @@ struct HostMesh {
   std::vector<uint64_t> t_cnt;          // byte s: largest member count of sub-stencil s
   std::vector<int32_t> t_st, t_sb;      // prefix sums of t_K and of the t_cnt bytes
   std::vector<int32_t> t_idx;           // [t_st[nt]][32] interleaved stencil entries
+  // reverse stencil: for each cell, the tile-layout positions (t_st[t] + k) 32 + lane of the
+  // stencil entries that reference it (real entries only), in increasing position
+  std::vector<int32_t> rs_ptr, rs_pos;
 };
 
 struct DeviceGeom;  // defined in the CUDA sources

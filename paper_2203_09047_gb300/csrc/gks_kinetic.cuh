@@ -4,18 +4,20 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace gks {
 
 #define GKS_HD __host__ __device__ __forceinline__
 
-__device__ __forceinline__ double k_exp(double x) { return exp(x); }
-__device__ __forceinline__ float k_exp(float x) { return expf(x); }
-__device__ __forceinline__ double k_erfc(double x) { return erfc(x); }
-__device__ __forceinline__ float k_erfc(float x) { return erfcf(x); }
-__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float k_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double k_abs(double x) { return fabs(x); }
-__device__ __forceinline__ float k_abs(float x) { return fabsf(x); }
+GKS_HD double k_exp(double x) { return exp(x); }
+GKS_HD float k_exp(float x) { return expf(x); }
+GKS_HD double k_erfc(double x) { return erfc(x); }
+GKS_HD float k_erfc(float x) { return erfcf(x); }
+GKS_HD double k_sqrt(double x) { return sqrt(x); }
+GKS_HD float k_sqrt(float x) { return sqrtf(x); }
+GKS_HD double k_abs(double x) { return fabs(x); }
+GKS_HD float k_abs(float x) { return fabsf(x); }
 
 // Moments <u^k>, <v^l>, <w^m>, <xi^(2x)> of a unit-density Maxwellian (u possibly over a
 // half line).

@@ -528,6 +528,28 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
         m.t_idx[((size_t)m.t_st[t] + k) * kTile + l] =
             k < Kc ? m.st_idx[m.st_ptr[c] + k] : (int32_t)(c < nc ? c : t * kTile);
     }
+  // 8. reverse stencil (counting sort by referenced cell, positions in increasing order)
+  m.rs_ptr.assign(nc + 1, 0);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int l = 0; l < kTile; ++l) {
+      const int64_t c = t * kTile + l;
+      if (c >= nc) continue;
+      for (int k = 0; k < m.st_ptr[c + 1] - m.st_ptr[c]; ++k)
+        ++m.rs_ptr[(m.t_idx[((size_t)m.t_st[t] + k) * kTile + l] & kCellMask) + 1];
+    }
+  for (int64_t c = 0; c < nc; ++c) m.rs_ptr[c + 1] += m.rs_ptr[c];
+  m.rs_pos.assign(m.rs_ptr[nc], 0);
+  {
+    std::vector<int32_t> fill(m.rs_ptr.begin(), m.rs_ptr.end() - 1);
+    for (int64_t t = 0; t < nt; ++t)
+      for (int k = 0; k < m.t_K[t]; ++k)
+        for (int l = 0; l < kTile; ++l) {
+          const int64_t c = t * kTile + l;
+          if (c >= nc || k >= m.st_ptr[c + 1] - m.st_ptr[c]) continue;
+          const size_t pos = ((size_t)m.t_st[t] + k) * kTile + l;
+          m.rs_pos[fill[m.t_idx[pos] & kCellMask]++] = (int32_t)pos;
+        }
+  }
   return GKS_OK;
 }
 

@@ -5,8 +5,6 @@
 #include <cmath>
 #include <cstdint>
 
-#pragma nv_diag_suppress 20011
-#pragma nv_diag_suppress 20014
 #include "gks_kinetic.cuh"
 
 namespace gks {

@@ -1,0 +1,127 @@
+"""The residual's vector-Jacobian product (gks_residual_vjp) on the GPU.
+
+Checked by the dot-product identity <gQ, dQ> = <gL, dL> + <gLt, dLt> against the oracle's
+forward-mode (dual-number) directional derivatives, against central differences of the GPU
+residual, and through a checkpointed S2O4 rollout against central differences.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import paper_2203_09047_gb300 as gks  # noqa: E402
+from paper_2203_09047_gb300 import build, inputs as I  # noqa: E402
+
+CASES = {
+    "smooth_zero": dict(flux_mode=0, tau_model=0),
+    "full_inviscid": dict(flux_mode=1, tau_model=1),
+    "full_viscous": dict(flux_mode=1, tau_model=2, mu=1e-3),
+    "smooth_viscous": dict(flux_mode=0, tau_model=2, mu=2e-3),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    gks.load_library()
+
+
+_cache = {}
+
+
+def mesh_pair(n=8, layers="hybrid8", bc=(0, 0, 0), lo=(0, 0, 0), hi=(2, 2, 2)):
+    key = (n, layers, bc, lo, hi)
+    if key not in _cache:
+        m = I.layered_box_mesh(n, layers, lo=lo, hi=hi, bc=bc)
+        _cache[key] = (m, oracle.Mesh(m))
+    return _cache[key]
+
+
+def _dot_test(m, om, Q, params, dt, seed):
+    gL, gLt, dQ = I.normal_directions(Q.shape, 3, seed)
+    S = gks.Solver(m, **params)
+    gQ = S.residual_vjp(Q, dt, gL, gLt).cpu().numpy()
+    _, _, dL, dLt = om.residual_jvp(oracle.params_vec(**params), Q, dQ, dt)
+    lhs = (gQ * dQ).sum()
+    rhs = (gL * dL).sum() + (gLt * dLt).sum()
+    return lhs, rhs
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_vjp_dot_product_with_oracle_jvp(case):
+    m, om = mesh_pair()
+    Q = I.perturbed_state(om.advection_average(), seed=31, amp=0.02)
+    lhs, rhs = _dot_test(m, om, Q, CASES[case], 0.01, seed=32)
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+
+
+def test_vjp_dot_product_reflecting_box():
+    m, om = mesh_pair(8, "hybrid8", bc=(1, 1, 1), lo=(-1, -1, -1), hi=(1, 1, 1))
+    q = np.array([0.8, 0.1, -0.05, 0.02, 1.1 / 0.4])
+    Q = I.perturbed_state(np.tile(q[:, None], (1, om.n_cells)), seed=33, amp=0.02)
+    lhs, rhs = _dot_test(m, om, Q, CASES["full_viscous"], 0.004, seed=34)
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
+
+
+def test_vjp_against_central_differences_and_deterministic():
+    m, om = mesh_pair()
+    Q = I.perturbed_state(om.advection_average(), seed=35, amp=0.02)
+    p = CASES["full_viscous"]
+    gL, gLt, d = I.normal_directions(Q.shape, 3, 36)
+    S = gks.Solver(m, **p)
+    gQ1 = S.residual_vjp(Q, 0.01, gL, gLt)
+    gQ2 = S.residual_vjp(Q, 0.01, gL, gLt)
+    assert torch.equal(gQ1, gQ2)
+    eps = 1e-6
+    Lp, Ltp = S.residual(Q + eps * d, 0.01)
+    Lm, Ltm = S.residual(Q - eps * d, 0.01)
+    fd = ((gL * (Lp - Lm).cpu().numpy()).sum() + (gLt * (Ltp - Ltm).cpu().numpy()).sum()) / (2 * eps)
+    got = (gQ1.cpu().numpy() * d).sum()
+    assert abs(got - fd) <= 1e-6 * abs(fd), (got, fd)
+
+
+def test_vjp_of_mixed_solver_is_fp64():
+    m, om = mesh_pair()
+    Q = I.perturbed_state(om.advection_average(), seed=37, amp=0.02)
+    p = CASES["smooth_zero"]
+    gL, gLt, _ = I.normal_directions(Q.shape, 3, 38)
+    g64 = gks.Solver(m, **p).residual_vjp(Q, 0.01, gL, gLt)
+    gmx = gks.Solver(m, precision=gks.GKS_PREC_MIXED, **p).residual_vjp(Q, 0.01, gL, gLt)
+    assert (g64 - gmx).norm() <= 1e-13 * g64.norm()
+
+
+def test_checkpointed_s2o4_rollout_gradient():
+    """Gradient of J = sum |Omega| rho^2 after 6 S2O4 steps (checkpoint every 2) through the
+    autograd wrapper, against central differences and the oracle's forward-mode rollout."""
+    from paper_2203_09047_gb300.autograd import s2o4_rollout
+    m, om = mesh_pair()
+    p = CASES["full_viscous"]
+    Q0 = I.perturbed_state(om.advection_average(), seed=39, amp=0.01)
+    vol = torch.from_numpy(om.cell_info()["vol"]).cuda()
+    S = gks.Solver(m, **p)
+    dt = 0.004
+    nsteps = 6
+
+    def J(Q):
+        QT = s2o4_rollout(Q, S, dt, nsteps, checkpoint_every=2)
+        return (vol * QT[0] ** 2).sum()
+
+    Qt = torch.from_numpy(Q0).cuda().requires_grad_(True)
+    J(Qt).backward()
+    grad = Qt.grad.detach().cpu().numpy()
+    dirs = I.normal_directions(Q0.shape, 3, 40)
+    with torch.no_grad():
+        for d in dirs:
+            eps = 1e-6
+            dd = torch.from_numpy(d).cuda()
+            fd = (J(Qt + eps * dd) - J(Qt - eps * dd)).item() / (2 * eps)
+            assert abs((grad * d).sum() - fd) <= 1e-6 * abs(fd)
+    # the oracle's tangent rollout for one direction
+    d = dirs[0]
+    QTo, dQTo = om.step_jvp(oracle.params_vec(**p), Q0, d, dt, nsteps)
+    jd = (2.0 * om.cell_info()["vol"] * QTo[0] * dQTo[0]).sum()
+    assert abs((grad * d).sum() - jd) <= 1e-9 * abs(jd)
