@@ -133,12 +133,29 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
 
   // phase 1: stencil differences, members split over the warps; the loops below are unrolled
   // so that several iterations' loads are in flight per warp
-#pragma unroll 2
-  for (int k = warp; k < K; k += kReconWarps) {
-    R dq[5];
-    stencil_delta(QA, __ldg(sidx + k * kTile), c0, dq);
+  for (int k0 = warp; k0 < K; k0 += 4 * kReconWarps) {
+    // four members per batch: all index loads, then all state loads, then the differences
+    int32_t e[4];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kTile + lane] = dq[v];
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u * kReconWarps;
+      e[u] = k < K ? __ldg(sidx + k * kTile) : -1;
+    }
+    Gq<R> g[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (e[u] >= 0) g[u].load(QA, e[u] & kCellMask);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e[u] < 0) continue;
+      const int fl = e[u] >> kFlipShift;
+      if (fl & 1) g[u].flip(1);
+      if (fl & 2) g[u].flip(2);
+      if (fl & 4) g[u].flip(3);
+      const int k = k0 + u * kReconWarps;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kTile + lane] = g[u].minus(c0, v);
+    }
   }
   __syncthreads();
 
