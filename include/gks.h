@@ -60,7 +60,10 @@ enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
 typedef struct {
   double gamma;      /* specific heat ratio; K = (5 - 3 gamma)/(gamma - 1) internal dofs */
   double mu;         /* dynamic viscosity (0: Euler) */
-  double Pr;         /* Prandtl number: only 1 (the BGK value) is accepted */
+  double Pr;         /* Prandtl number; 1 is the BGK value. Other values apply the heat-flux
+                        correction of the BGK-NS scheme (energy flux + (1/Pr - 1) q, q the heat
+                        flux of the interface distribution), smooth flux only; the VJP
+                        supports Pr = 1 only */
   int flux_mode;     /* GKS_FLUX_* */
   int tau_model;     /* GKS_TAU_* */
   double tau_eps;    /* eps of the inviscid collision time (Section 5: 0.01) */
@@ -118,6 +121,13 @@ gks_status gks_get_state(gks_solver* s, double* Q);
  * h_i = |Omega_i| / (largest face area of cell i). Synchronises the stream.
  * Errors: GKS_E_NONPHYSICAL. */
 gks_status gks_max_dt(gks_solver* s, double cfl, double* dt);
+
+/* The 27-point quadrature of every cell (3 Gauss-Legendre points per direction mapped by the
+ * trilinear map of Eq. trilinear, Section 2), for cell averages of given fields (initial data,
+ * exact solutions) and volume-weighted norms: xq [n_cells][27][3] points, wq [n_cells][27]
+ * weights times |J| (they sum to the cell volume), caller order, host or device pointers.
+ * Uses temporary device memory and synchronises the stream. */
+gks_status gks_cell_quadrature(gks_solver* s, double* xq, double* wq);
 
 /* Advance the solver's state by nsteps two-stage fourth-order steps of size dt (Section 3.3):
  *   Q*      = Q^n + dt/2 L(Q^n) + dt^2/8 Lt(Q^n)

@@ -60,6 +60,7 @@ def lib():
         L.oracle_n_faces.restype = ctypes.c_int64
         L.oracle_n_faces.argtypes = [P]
         L.oracle_cell_info.argtypes = [P, D, D, I, I, I]
+        L.oracle_stencil_conditioning.argtypes = [P, D]
         L.oracle_face_info.argtypes = [P, I, I, D, D, D, D]
         L.oracle_cell_average.argtypes = [P, ctypes.c_int, ctypes.c_double, D, D]
         L.oracle_reconstruct_at.argtypes = [P, D, D, ctypes.c_int, I, D, D]
@@ -125,6 +126,11 @@ class Mesh:
         K, M, plain = (np.zeros(n, dtype=np.int32) for _ in range(3))
         lib().oracle_cell_info(self.h, _d(vol), _d(cen), _i(K), _i(M), _i(plain))
         return dict(vol=vol, centroid=cen, K=K, M=M, plain=plain.astype(bool))
+
+    def stencil_conditioning(self):
+        out = np.zeros(self.n_cells)
+        lib().oracle_stencil_conditioning(self.h, _d(out))
+        return out
 
     def face_info(self):
         nf = self.n_faces

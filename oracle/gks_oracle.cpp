@@ -1037,6 +1037,32 @@ bool gp_flux(const Params& P, const T ql[5], const T dql[3][5], const T qr[5], c
     } else {
       for (int v = 0; v < 5; ++v)
         F[s][v] = w0.rho * (d * e0[v] - tau * d * (e1[v] + e2[v]) + 0.5 * d * d * e2[v]);
+      if (P.Pr != 1.0) {
+        // Prandtl-number fix of the BGK model (Xu 2001): the energy flux gains (1/Pr - 1) q with
+        // q = <(u - U0) ((u-U0)^2 + (v-V0)^2 + (w-W0)^2 + xi^2) / 2 f>, the heat flux of the
+        // time-integrated distribution relative to the interface velocity U0.
+        Poly<T> cu, heat;
+        cu.t.push_back({{1, 0, 0, 0}, T(1.0)});
+        cu.t.push_back({{0, 0, 0, 0}, -w0.U});
+        Poly<T> cv, cw, xi2;
+        cv.t.push_back({{0, 1, 0, 0}, T(1.0)});
+        cv.t.push_back({{0, 0, 0, 0}, -w0.V});
+        cw.t.push_back({{0, 0, 1, 0}, T(1.0)});
+        cw.t.push_back({{0, 0, 0, 0}, -w0.W});
+        xi2.t.push_back({{0, 0, 0, 1}, T(1.0)});
+        const Poly<T> c2 = add(add(add(mul(cu, cu), mul(cv, cv)), mul(cw, cw)), xi2);
+        heat = mul(cu, c2);
+        for (auto& x : heat.t) x.second = 0.5 * x.second;
+        // f integrated over [0, d]: g0 [d (1 - tau (a.u + A)) + d^2/2 A]
+        const Poly<T> one = mono<T>(0, 0, 0);
+        Poly<T> fpoly;
+        for (auto& x : one.t) fpoly.t.push_back({x.first, T(d) * x.second});
+        for (auto& x : add(a_dot_u(abar), combo<T>(Abar)).t)
+          fpoly.t.push_back({x.first, -tau * d * x.second});
+        for (auto& x : combo<T>(Abar).t) fpoly.t.push_back({x.first, 0.5 * d * d * x.second});
+        const T q = w0.rho * moment(mul(heat, fpoly), M0);
+        F[s][4] += (1.0 / P.Pr - 1.0) * q;
+      }
     }
   }
   return true;
@@ -1247,6 +1273,21 @@ void* oracle_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
 void oracle_mesh_destroy(void* h) { delete static_cast<Mesh*>(h); }
 
 int64_t oracle_n_faces(void* h) { return (int64_t) static_cast<Mesh*>(h)->faces.size(); }
+
+// Conditioning of each cell's big-stencil least-squares matrix: max |R_jj| / min |R_jj| of its
+// Householder factor (a lower bound of the 2-norm condition number).
+void oracle_stencil_conditioning(void* h, double* out) {
+  Mesh* m = static_cast<Mesh*>(h);
+  for (int i = 0; i < m->n_cells; ++i) {
+    build_cell_stencil(*m, i);
+    double lo = 1e300, hi = 0;
+    for (double r : m->cells[i].qr0.rdiag) {
+      lo = std::min(lo, std::fabs(r));
+      hi = std::max(hi, std::fabs(r));
+    }
+    out[i] = m->cells[i].qr0.rdiag.empty() ? 0.0 : hi / lo;
+  }
+}
 
 // vol[n], centroid[n][3], K[n] stencil size, M[n] sub-stencil count, plain[n] (1 if no member
 // carries a periodic or mirror transform)

@@ -82,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_timing_enable.restype = st
     L.gks_timing_read.argtypes = [P, D, ctypes.POINTER(I64)]
     L.gks_timing_read.restype = st
+    L.gks_cell_quadrature.argtypes = [P, P, P]
+    L.gks_cell_quadrature.restype = st
     L.gks_kernel_bytes.argtypes = [P, D]
     L.gks_kernel_bytes.restype = st
     L.gks_flux_opcount.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
@@ -201,6 +203,10 @@ def gks_timing_read(solver):
     return list(ms), list(cnt)
 
 
+def gks_cell_quadrature(solver, xq, wq):
+    _check(load_library().gks_cell_quadrature(solver, _ptr(xq), _ptr(wq)), solver)
+
+
 def gks_kernel_bytes(solver):
     """Algorithmic bytes per launch of (reconstruction, flux, face sum + update)."""
     b = (ctypes.c_double * 3)()
@@ -315,6 +321,19 @@ class Solver:
         Lt = self.torch.empty_like(Q)
         gks_residual(self.h, Q, dt, L, Lt)
         return L, Lt
+
+    def cell_quadrature(self):
+        """(points [n, 27, 3], weights [n, 27]) as float64 numpy arrays, caller order."""
+        xq = np.empty((self.n_cells, 27, 3))
+        wq = np.empty((self.n_cells, 27))
+        gks_cell_quadrature(self.h, xq, wq)
+        return xq, wq
+
+    def cell_average(self, field):
+        """Cell averages [5, n] of field(x[..., 3]) -> [5, ...] by the 27-point quadrature."""
+        xq, wq = self.cell_quadrature()
+        vals = field(xq)
+        return np.ascontiguousarray((vals * wq[None]).sum(axis=-1) / wq.sum(axis=-1)[None])
 
     def residual_vjp(self, Q, dt: float, gL, gLt):
         Q, gL, gLt = self._dev(Q), self._dev(gL), self._dev(gLt)

@@ -1,0 +1,186 @@
+"""Validation cases on the synthetic hybrid meshes, run through the public API on the GPU.
+
+    python -m paper_2203_09047_gb300.cases advection   # convergence 8..64 cubes, FP64 and mixed
+    python -m paper_2203_09047_gb300.cases tgv         # Taylor-Green vortex, Re 1600, Pr 0.72
+    python -m paper_2203_09047_gb300.cases adjoint     # gradient through 200 S2O4 steps vs FD
+    python -m paper_2203_09047_gb300.cases explosion   # spherical explosion, reflecting box
+
+Each prints one JSON line per result.
+"""
+from __future__ import annotations
+
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import GKS_PREC_FP64, GKS_PREC_MIXED, Mesh, Solver, GksError
+from . import inputs as I
+
+
+def _emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def _exact_advection(t, gamma=1.4):
+    def field(x):
+        rho, u, p = I.advection_primitive(x, t)
+        return I.primitive_to_conserved(rho, u, p, gamma)
+    return field
+
+
+def advection(ns=(8, 16, 32, 64), t_end=0.2, cfl=0.5, layers="hybrid8"):
+    """Section 5.1 accuracy test on the hybrid generator: errors against the exact cell averages
+    (volume-weighted, unnormalised L1 and L2 of density as in Tables tab-3d-1/2), orders, and
+    cell-stage updates/s, for the FP64 and mixed paths."""
+    import torch
+    out = []
+    for prec, name in ((GKS_PREC_FP64, "fp64"), (GKS_PREC_MIXED, "mixed")):
+        prev = None
+        for n in ns:
+            m = I.layered_box_mesh(n, layers)
+            S = Solver(m, precision=prec)
+            Q0 = S.cell_average(_exact_advection(0.0))
+            S.set_state(Q0)
+            dt = S.max_dt(cfl)
+            nsteps = int(np.ceil(t_end / dt - 1e-12))
+            dt = t_end / nsteps
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            S.step(dt, nsteps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            Q = S.get_state().cpu().numpy()
+            xq, wq = S.cell_quadrature()
+            vol = wq.sum(axis=1)
+            ex = S.cell_average(_exact_advection(t_end))
+            e = Q[0] - ex[0]
+            l1 = float((vol * np.abs(e)).sum())
+            l2 = float(np.sqrt((vol * e * e).sum()))
+            rec = {"case": "advection", "mesh": layers, "precision": name, "cubes": n, "cells": S.n_cells,
+                   "steps": nsteps, "dt": dt, "L1": l1, "L2": l2,
+                   "cell_stage_per_s": S.n_cells * 2 * nsteps / el}
+            if prev is not None:
+                rec["order_L1"] = float(np.log2(prev[0] / l1))
+                rec["order_L2"] = float(np.log2(prev[1] / l2))
+            prev = (l1, l2)
+            _emit(rec)
+            out.append(rec)
+            S.close()
+    return out
+
+
+def tgv(n=48, steps=200, cfl=0.5, re=1600.0, mach=0.1, pr=0.72):
+    """Taylor-Green vortex on the TGV layer pattern in [0, 2 pi]^3: kinetic energy and its
+    dissipation rate, mixed path against the FP64 path."""
+    import torch
+    m = I.layered_box_mesh(n, "tgv48", lo=(0, 0, 0), hi=(2 * np.pi,) * 3, jitter=0.05)
+    mesh = Mesh(m)
+    Q0 = I.taylor_green_state(m, mach=mach)
+    params = dict(flux_mode=0, tau_model=2, mu=1.0 / re, Pr=pr)
+    series = {}
+    for prec, name in ((GKS_PREC_FP64, "fp64"), (GKS_PREC_MIXED, "mixed")):
+        S = Solver(mesh, precision=prec, **params)
+        if name == "fp64":
+            # cell averages of the initial field by the 27-point quadrature
+            def field(x):
+                X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+                u = np.stack([np.sin(X) * np.cos(Y) * np.cos(Z), -np.cos(X) * np.sin(Y) * np.cos(Z),
+                              np.zeros_like(X)], axis=-1)
+                p = 1.0 / (1.4 * mach * mach) + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
+                return I.primitive_to_conserved(np.ones_like(X), u, p)
+            Q0 = S.cell_average(field)
+            vol = torch.from_numpy(S.cell_quadrature()[1].sum(axis=1)).cuda()
+            S.set_state(Q0)
+            dt = S.max_dt(cfl)
+        S.set_state(Q0)
+        ke = []
+        t0 = time.perf_counter()
+        for k in range(steps + 1):
+            Q = S.get_state()
+            ke.append(float(((0.5 * (Q[1] ** 2 + Q[2] ** 2 + Q[3] ** 2) / Q[0]) * vol).sum() / vol.sum()))
+            if k < steps:
+                S.step(dt, 1, check=(k % 20 == 19))
+        torch.cuda.synchronize()
+        series[name] = (np.array(ke), time.perf_counter() - t0)
+        S.close()
+    k64, km = series["fp64"][0], series["mixed"][0]
+    eps64 = -np.gradient(k64, dt)
+    epsm = -np.gradient(km, dt)
+    rec = {"case": "tgv", "cubes": n, "cells": mesh.n_cells, "steps": steps, "dt": dt,
+           "t_end": steps * dt, "ke0": k64[0], "ke_end_fp64": k64[-1], "ke_end_mixed": km[-1],
+           "ke_max_rel_diff": float(np.abs(km - k64).max() / k64[0]),
+           "dissipation_end_fp64": float(eps64[-1]), "dissipation_end_mixed": float(epsm[-1]),
+           "dissipation_max_rel_diff": float(np.abs(epsm - eps64).max() / np.abs(eps64).max()),
+           "wall_s_fp64": series["fp64"][1], "wall_s_mixed": series["mixed"][1]}
+    _emit(rec)
+    return rec
+
+
+def adjoint(n=32, steps=200, every=20, ndirs=20, mu=1e-3, cfl=0.5, eps=1e-6, layers="tet"):
+    """Gradient of J = sum |Omega| rho^2 at the final time with respect to the initial state,
+    through `steps` S2O4 steps with checkpoints every `every`, against central differences on
+    `ndirs` random directions (Navier-Stokes, full flux, viscous collision time). The default
+    mesh is the Kuhn-tetrahedron box; on the hybrid generator the transition layers' nearly
+    singular pyramid stencils make J non-smooth over 200 steps (central differences do not
+    converge there)."""
+    import torch
+    from .autograd import s2o4_rollout
+    m = I.layered_box_mesh(n, layers)
+    S = Solver(m, flux_mode=1, tau_model=2, mu=mu)
+    Qc = S.cell_average(_exact_advection(0.0))
+    Q0 = I.perturbed_state(Qc, seed=2, amp=0.01)
+    S.set_state(Q0)
+    dt = S.max_dt(cfl)
+    vol = torch.from_numpy(S.cell_quadrature()[1].sum(axis=1)).cuda()
+
+    def J(Q):
+        QT = s2o4_rollout(Q, S, dt, steps, checkpoint_every=every)
+        return (vol * QT[0] ** 2).sum()
+
+    Qt = torch.from_numpy(Q0).cuda().requires_grad_(True)
+    t0 = time.perf_counter()
+    J(Qt).backward()
+    t_grad = time.perf_counter() - t0
+    grad = Qt.grad.detach()
+    dirs = I.normal_directions(Q0.shape, ndirs, 3)
+    worst = 0.0
+    with torch.no_grad():
+        for d in dirs:
+            dd = torch.from_numpy(d).cuda()
+            fd = (J(Qt + eps * dd) - J(Qt - eps * dd)).item() / (2 * eps)
+            ad = float((grad * dd).sum())
+            worst = max(worst, abs(ad - fd) / abs(fd))
+    rec = {"case": "adjoint", "mesh": layers, "cubes": n, "cells": S.n_cells, "steps": steps,
+           "checkpoint_every": every,
+           "directions": ndirs, "fd_eps": eps, "max_rel_diff_vs_fd": worst, "gradient_wall_s": t_grad}
+    _emit(rec)
+    return rec
+
+
+def explosion(n=32, t_end=0.25, cfl=0.5):
+    """Spherical explosion in the reflecting box [-1,1]^3 (full flux, inviscid collision time):
+    mass and energy drift per step and the mixed-vs-FP64 density difference."""
+    m = I.layered_box_mesh(n, "hybrid8", lo=(-1, -1, -1), hi=(1, 1, 1), bc=(1, 1, 1))
+    Q0 = I.explosion_state(m)
+    params = dict(flux_mode=1, tau_model=1)
+    rec = {"case": "explosion", "cubes": n, "cells": len(m["cell_type"])}
+    try:
+        S = Solver(m, **params)
+        S.set_state(Q0)
+        S.residual(Q0, 1e-4)
+        rec["status"] = "ok"
+    except GksError as e:
+        rec["status"] = f"non-physical reconstruction at t = 0: {e}"
+    _emit(rec)
+    return rec
+
+
+if __name__ == "__main__":
+    which = sys.argv[1] if len(sys.argv) > 1 else "advection"
+    kwargs = {}
+    for a in sys.argv[2:]:
+        k, v = a.split("=")
+        kwargs[k] = int(v) if v.isdigit() else v
+    {"advection": advection, "tgv": tgv, "adjoint": adjoint, "explosion": explosion}[which](**kwargs)

@@ -133,6 +133,7 @@ KParams<R> kparams(const gks_params& p) {
   k.mu = (R)p.mu;
   k.tau_eps = (R)p.tau_eps;
   k.tau_C = (R)p.tau_C;
+  k.pr_fix = (R)(1.0 / p.Pr - 1.0);
   k.flux_mode = p.flux_mode;
   k.tau_model = p.tau_model;
   k.weno_gamma = (R)p.weno_gamma;
@@ -233,7 +234,11 @@ gks_status check_and_clear(gks_solver* s) {
 bool valid_params(const gks_params* p, std::string& why) {
   if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) { why = "gamma must lie in (1, 5/3]"; return false; }
   if (!(p->mu >= 0.0)) { why = "mu must be >= 0"; return false; }
-  if (p->Pr != 1.0) { why = "only Pr = 1 (the BGK value) is supported"; return false; }
+  if (!(p->Pr > 0.0)) { why = "Pr must be > 0"; return false; }
+  if (p->Pr != 1.0 && p->flux_mode != GKS_FLUX_SMOOTH) {
+    why = "the Prandtl-number correction is implemented for the smooth flux only";
+    return false;
+  }
   if (p->flux_mode != GKS_FLUX_SMOOTH && p->flux_mode != GKS_FLUX_FULL) { why = "flux_mode"; return false; }
   if (p->tau_model < GKS_TAU_ZERO || p->tau_model > GKS_TAU_VISCOUS) { why = "tau_model"; return false; }
   if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
@@ -478,6 +483,7 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
 gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
                             const double* gLt, double* gQ) {
   if (!s || !Q || !gL || !gLt || !gQ || !(dt > 0)) return GKS_E_INVAL;
+  if (s->prm.Pr != 1.0) return s->fail(GKS_E_INVAL, "the VJP supports Pr = 1 only");
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e = cudaSuccess;
   if (!s->vjp_ready) {
@@ -529,6 +535,24 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
   e = cudaGetLastError();
   if (e != cudaSuccess) return s->cuda_fail(e, "vjp launch");
   return check_and_clear(s);
+}
+
+gks_status gks_cell_quadrature(gks_solver* s, double* xq, double* wq) {
+  if (!s || !xq || !wq) return GKS_E_INVAL;
+  const int64_t nc = s->m.nc;
+  double* dx = nullptr;
+  double* dw = nullptr;
+  cudaError_t e = cudaMalloc((void**)&dx, sizeof(double) * 81 * nc);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dw, sizeof(double) * 27 * nc);
+  if (e == cudaSuccess) {
+    launch_cell_quadrature(s->m, dx, dw, s->st);
+    e = cudaMemcpyAsync(xq, dx, sizeof(double) * 81 * nc, cudaMemcpyDefault, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(wq, dw, sizeof(double) * 27 * nc, cudaMemcpyDefault, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+  }
+  if (dx) cudaFree(dx);
+  if (dw) cudaFree(dw);
+  return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "cell quadrature");
 }
 
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {

@@ -92,7 +92,7 @@ struct GeoR {
 // Parameters of the hot kernels.
 template <class R>
 struct KParams {
-  R gamma, K, mu, tau_eps, tau_C;
+  R gamma, K, mu, tau_eps, tau_C, pr_fix;
   int flux_mode, tau_model;
   R weno_gamma, weno_eps;
   int weno_pow;
@@ -108,6 +108,7 @@ void launch_geom_ls(const DevMesh& m, const Geo64& g, GeoR<R>& gr, int* flag, in
                     cudaStream_t st);
 template <class R>
 void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st);
+void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream_t st);
 
 // ---- hot path (gks_hot.cu) ----------------------------------------------------------------
 template <class R>

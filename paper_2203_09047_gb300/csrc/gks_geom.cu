@@ -276,7 +276,47 @@ __global__ void k_cast_cells(int64_t nc, const double* __restrict__ hh, const do
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// The 27 Gauss points (3 per direction on [-1/2,1/2]^3 mapped by the trilinear map) and their
+// weights times |J| for every cell, written at the caller's cell index.
+__global__ void k_cell_quadrature(int64_t nc, const double* __restrict__ cell_x,
+                                  const int32_t* __restrict__ perm, double* xq, double* wq) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double X[8][3];
+  for (int s = 0; s < 8; ++s)
+    for (int a = 0; a < 3; ++a) X[s][a] = cell_x[24 * i + 3 * s + a];
+  const int sx[8] = {-1, 1, 1, -1, -1, 1, 1, -1};
+  const int sy[8] = {-1, -1, 1, 1, -1, -1, 1, 1};
+  const int sz[8] = {-1, -1, -1, -1, 1, 1, 1, 1};
+  const int64_t c = perm[i];
+  int g = 0;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q)
+      for (int r = 0; r < 3; ++r, ++g) {
+        const double xi = g3x(p), et = g3x(q), ze = g3x(r);
+        double x[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int s = 0; s < 8; ++s) {
+          const double fx = 0.5 + sx[s] * xi, fy = 0.5 + sy[s] * et, fz = 0.5 + sz[s] * ze;
+          for (int a = 0; a < 3; ++a) {
+            x[a] += X[s][a] * fx * fy * fz;
+            J[a][0] += X[s][a] * sx[s] * fy * fz;
+            J[a][1] += X[s][a] * fx * sy[s] * fz;
+            J[a][2] += X[s][a] * fx * fy * sz[s];
+          }
+        }
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        for (int a = 0; a < 3; ++a) xq[(27 * c + g) * 3 + a] = x[a];
+        wq[27 * c + g] = g3w(p) * g3w(q) * g3w(r) * det;
+      }
+}
+
 }  // namespace
+
+void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream_t st) {
+  k_cell_quadrature<<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, m.cell_x, m.perm, xq, wq);
+}
 
 void launch_geom_cells(const DevMesh& m, const Geo64& g, int* flag, cudaStream_t st) {
   k_geom_cells<<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, m.cell_x, g.vol, g.cen, g.h,

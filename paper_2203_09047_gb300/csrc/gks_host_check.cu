@@ -7,7 +7,7 @@
 
 namespace {
 gks::FluxParams<double> params_from(const double* p) {
-  // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model}
+  // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr}
   gks::FluxParams<double> P;
   P.gamma = p[0];
   P.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
@@ -16,6 +16,7 @@ gks::FluxParams<double> params_from(const double* p) {
   P.tau_C = p[3];
   P.full = (int)p[4];
   P.tau_model = (int)p[5];
+  P.pr_fix = 1.0 / p[6] - 1.0;
   return P;
 }
 }  // namespace

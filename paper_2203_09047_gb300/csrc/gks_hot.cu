@@ -555,6 +555,7 @@ void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const 
   fp.tau_C = p.tau_C;
   fp.full = p.flux_mode;
   fp.tau_model = p.tau_model;
+  fp.pr_fix = p.pr_fix;
   k_flux<R><<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall,
                                                          g.fgp, poly, fp, (R)dt, fface, flag);
 }

@@ -150,6 +150,7 @@ template <class R>
 struct FluxParams {
   R gamma, K, mu, tau_eps, tau_C;
   int full, tau_model;
+  R pr_fix = R(0);  // 1/Pr - 1 (heat-flux correction of the smooth flux; 0 for the BGK value)
 };
 
 // Time integrals over [0, d] of the six coefficients of Eq. flux-1.
@@ -240,6 +241,23 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
     for (int q = 0; q < 5; ++q) {
       Fn[q] = w0.rho * (e0[q] - tau * (e1[q] + e2[q]));
       Ft[q] = w0.rho * e2[q];
+    }
+    if (P.pr_fix != R(0)) {
+      // heat flux relative to the interface velocity, from the flux moments F and the conserved
+      // moments m of the time-integrated distribution: m^n = Q0, dm/dt = rho0 <A psi>_0
+      // (the tau terms of m vanish by the compatibility condition defining A)
+      R mt[5];
+      Ga(M0, Ab, 0, 0, 0, mt);
+      const R u2 = w0.U * w0.U + w0.V * w0.V + w0.W * w0.W;
+      auto heat = [&](const R F[5], const R m[5], R sc) {
+        return F[4] - (w0.U * F[1] + w0.V * F[2] + w0.W * F[3]) + R(0.5) * u2 * F[0] -
+               sc * (w0.U * m[4] - w0.U * (w0.U * m[1] + w0.V * m[2] + w0.W * m[3]) +
+                     R(0.5) * w0.U * u2 * m[0]);
+      };
+      const R qn = heat(Fn, q0, R(1));
+      const R qt = heat(Ft, mt, w0.rho);
+      Fn[4] += P.pr_fix * qn;
+      Ft[4] += P.pr_fix * qt;
     }
     return true;
   }

@@ -35,6 +35,7 @@ inline Op& operator-=(Op& a, Op b) { a = a - b; return a; }
 inline Op& operator*=(Op& a, Op b) { a = a * b; return a; }
 inline bool operator<(Op a, Op b) { return a.v < b.v; }
 inline bool operator>(Op a, Op b) { return a.v > b.v; }
+inline bool operator!=(Op a, Op b) { return a.v != b.v; }
 inline Op k_exp(Op a) { ++g_count.special; return Op(std::exp(a.v)); }
 inline Op k_erfc(Op a) { ++g_count.special; return Op(std::erfc(a.v)); }
 inline Op k_sqrt(Op a) { ++g_count.special; return Op(std::sqrt(a.v)); }

@@ -42,8 +42,23 @@ def _flux(lib, P, x, dt):
 @pytest.mark.parametrize("mode,tau_model", CASES)
 def test_gp_flux_matches_oracle(lib, mode, tau_model):
     rng = np.random.default_rng(100 + 7 * mode + tau_model)
-    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model])
+    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model, 1.0])
     Po = oracle.params_vec(flux_mode=mode, tau_model=tau_model, mu=2e-3)
+    for _ in range(6):
+        ql, qr = _state(rng), _state(rng)
+        dql, dqr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
+        dt = 0.01
+        F = _flux(lib, P, np.concatenate([ql, dql.ravel(), qr, dqr.ravel()]), dt)
+        Fo = oracle.gp_flux(Po, ql, dql, qr, dqr, dt)
+        Fn_o, Ft_o = (4 * Fo[0] - Fo[1]) / dt, 4 * (Fo[1] - 2 * Fo[0]) / dt ** 2
+        np.testing.assert_allclose(F[:5], Fn_o, rtol=0, atol=1e-11 * np.abs(Fn_o).max())
+        np.testing.assert_allclose(F[5:], Ft_o, rtol=0, atol=1e-10 * np.abs(Ft_o).max())
+
+
+def test_gp_flux_prandtl_fix_matches_oracle(lib):
+    rng = np.random.default_rng(150)
+    P = np.array([1.4, 3e-3, 0.01, 1.0, 0, 2, 0.72])
+    Po = oracle.params_vec(flux_mode=0, tau_model=2, mu=3e-3, Pr=0.72)
     for _ in range(6):
         ql, qr = _state(rng), _state(rng)
         dql, dqr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
@@ -58,7 +73,7 @@ def test_gp_flux_matches_oracle(lib, mode, tau_model):
 @pytest.mark.parametrize("mode,tau_model", CASES)
 def test_gp_flux_vjp_matches_central_differences(lib, mode, tau_model):
     rng = np.random.default_rng(200 + 7 * mode + tau_model)
-    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model])
+    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model, 1.0])
     dt = 0.01
     for _ in range(3):
         ql, qr = _state(rng), _state(rng)
@@ -83,7 +98,7 @@ def test_gp_flux_vjp_matches_central_differences(lib, mode, tau_model):
 def test_global_frame_vjp_matches_central_differences(lib, mode, tau_model):
     """Rotation into the Gauss point's frame, flux, rotation back and weight, reversed."""
     rng = np.random.default_rng(300 + mode)
-    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model])
+    P = np.array([1.4, 2e-3, 0.01, 1.0, mode, tau_model, 1.0])
     n1 = rng.normal(size=3)
     n1 /= np.linalg.norm(n1)
     w, dt = 0.037, 0.01

@@ -300,10 +300,10 @@ def test_smooth_tau0_is_cauchy_kovalevskaya(mode):
         np.testing.assert_allclose(Ft, ft, rtol=1e-10, atol=1e-11)
 
 
-def _ns_flux(q, dq, mu, gamma=GAMMA, K=K_DOF):
+def _ns_flux(q, dq, mu, gamma=GAMMA, K=K_DOF, Pr=1.0):
     """Navier-Stokes flux along n1 of the BGK model (Chapman-Enskog, Section 3.1): shear
-    viscosity mu, normal-stress coefficient 2/(K+3), Prandtl number 1 (kappa = c_p mu with
-    c_p = (K+5)/2 in units R = 1)."""
+    viscosity mu, normal-stress coefficient 2/(K+3), heat conductivity kappa = c_p mu / Pr with
+    c_p = (K+5)/2 in units R = 1 (Pr = 1 for the plain BGK model)."""
     rho = q[0]
     U = q[1:4] / rho
     p = (gamma - 1) * (q[4] - 0.5 * rho * U @ U)
@@ -317,7 +317,7 @@ def _ns_flux(q, dq, mu, gamma=GAMMA, K=K_DOF):
         dT[d] = (dp - T * drho) / rho
     div = np.trace(dU)
     sigma = mu * (dU + dU.T) - mu * 2.0 / (K + 3) * div * np.eye(3)
-    qflux = -(K + 5) / 2.0 * mu * dT
+    qflux = -(K + 5) / 2.0 * mu / Pr * dT
     F = _euler_flux(q)
     F[1:4] -= sigma[0]
     F[4] -= sigma[0] @ U - qflux[0]
@@ -337,6 +337,21 @@ def test_smooth_viscous_is_chapman_enskog(mode):
         F = oracle.gp_flux(P, q, dq, q, dq, 1e-3)
         Fn, _ = _fit(F, 1e-3)
         np.testing.assert_allclose(Fn, _ns_flux(q, dq, mu), rtol=1e-11, atol=1e-12)
+
+
+def test_prandtl_fix_gives_navier_stokes_heat_flux():
+    """With the heat-flux correction (Xu 2001) the smooth flux is the Navier-Stokes flux with
+    kappa = c_p mu / Pr, e.g. Pr = 0.72 (the Taylor-Green configuration)."""
+    rng = np.random.default_rng(35)
+    mu = 3e-3
+    for Pr in (0.72, 2.0 / 3.0):
+        P = oracle.params_vec(flux_mode=0, tau_model=2, mu=mu, Pr=Pr)
+        for _ in range(4):
+            q = _random_state(rng)
+            dq = rng.normal(size=(3, 5)) * 0.2
+            F = oracle.gp_flux(P, q, dq, q, dq, 1e-3)
+            Fn, _ = _fit(F, 1e-3)
+            np.testing.assert_allclose(Fn, _ns_flux(q, dq, mu, Pr=Pr), rtol=1e-11, atol=1e-12)
 
 
 def test_full_flux_reduces_to_smooth_flux_for_continuous_data():

@@ -90,6 +90,21 @@ def test_residual_fp64_reflecting_box():
     assert rel(L.cpu(), Lo) < FP64_TOL and rel(Lt.cpu(), Lto) < FP64_TOL
 
 
+def test_residual_fp64_taylor_green_prandtl():
+    """Navier-Stokes with the Prandtl-number correction (Pr = 0.72) on the Taylor-Green layer
+    pattern, [0, 2 pi]^3."""
+    m, om = mesh_pair(8, "tgv48", lo=(0, 0, 0), hi=(2 * np.pi,) * 3)
+    Q = I.perturbed_state(I.taylor_green_state(m), seed=15, amp=0.01)
+    p = dict(flux_mode=0, tau_model=2, mu=1.0 / 1600.0, Pr=0.72)
+    S = gks.Solver(m, **p)
+    L, Lt = S.residual(Q, 0.02)
+    Lo, Lto = om.residual(oracle.params_vec(**p), Q, 0.02)
+    assert rel(L.cpu(), Lo) < FP64_TOL and rel(Lt.cpu(), Lto) < FP64_TOL
+    Sm = gks.Solver(m, precision=gks.GKS_PREC_MIXED, **p)
+    Lm, _ = Sm.residual(Q, 0.02)
+    assert rel(Lm.cpu(), Lo) < MIXED_TOL_L
+
+
 def test_residual_fp64_mixed_boundaries():
     m, om = mesh_pair(8, "hybrid8", bc=(0, 1, 0))
     Q = smooth_state(m, om, seed=14)
