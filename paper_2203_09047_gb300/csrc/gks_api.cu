@@ -182,7 +182,7 @@ void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode
                 double* Lt, double* Qn, double* Qs) {
   const KParams<R> kp = kparams<R>(s->prm);
   int t = s->tick(0);
-  launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->st);
+  launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st);
   s->tock(t);
   t = s->tick(1);
   launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
@@ -226,6 +226,8 @@ gks_status check_and_clear(gks_solver* s) {
     cudaMemsetAsync(s->flag, 0, sizeof(int), s->st);
     if (f & kErrNonphysical)
       return s->fail(GKS_E_NONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN)");
+    if (f & kErrTimeout)
+      return s->fail(GKS_E_TIMEOUT, "an asynchronous copy did not complete within its wait limit");
     return s->fail(GKS_E_CUDA, "device status " + std::to_string(f));
   }
   return GKS_OK;
@@ -356,10 +358,33 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.t_st, h.t_st)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_sb, h.t_sb)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_idx, h.t_idx)) != cudaSuccess) return bad("upload");
+  // tile ranges by the kind of each tile's first cell (at most one per kind: cells are ordered
+  // by kind first); a new range is opened only while slots remain, else the last one grows
+  for (int64_t t = 0; t < h.n_tiles; ++t) {
+    TileRanges& r = m.rr;
+    const int kind = h.type[t * kTile];
+    if (r.n == 0 || (kind != h.type[r.t0[r.n - 1] * kTile] && r.n < kMaxTileRanges)) {
+      r.t0[r.n] = t;
+      r.t1[r.n] = t;
+      r.K[r.n] = r.S[r.n] = r.M[r.n] = 0;
+      ++r.n;
+    }
+    int S = 0, M = 0;
+    for (int q = 0; q < kMaxSub; ++q) {
+      const int c = (int)((h.t_cnt[t] >> (8 * q)) & 0xffu);
+      S += c;
+      if (c) M = q + 1;
+    }
+    r.t1[r.n - 1] = t + 1;
+    r.K[r.n - 1] = std::max(r.K[r.n - 1], h.t_K[t]);
+    r.S[r.n - 1] = std::max(r.S[r.n - 1], S);
+    r.M[r.n - 1] = std::max(r.M[r.n - 1], M);
+  }
   if ((e = supload(s, &s->rs_ptr, h.rs_ptr)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &s->rs_pos, h.rs_pos)) != cudaSuccess) return bad("upload");
   const int64_t nc = m.nc, nf = m.nf;
   if ((e = salloc(s, &s->g.vol, nc)) != cudaSuccess) return bad("alloc");
+  if ((e = salloc(s, &s->g.ivol, nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.cen, 3 * nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.h, nc)) != cudaSuccess) return bad("alloc");
   if ((e = salloc(s, &s->g.mom, 6 * nc)) != cudaSuccess) return bad("alloc");
@@ -526,7 +551,7 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
   launch_permute_in<double>(nc, s->m.perm, s->tmp, s->vgLt, (double*)nullptr, s->st);
   // forward reconstruction in FP64, then the reverse passes
   const KParams<double> kp = kparams<double>(s->prm);
-  launch_recon<double>(s->m, s->gv, kp, s->vQA, s->vpoly, s->st);
+  launch_recon<double>(s->m, s->gv, kp, s->vQA, s->vpoly, s->flag, s->st);
   launch_vjp(s->m, s->g, s->gv, kp, s->vQA, s->vpoly, s->vgL, s->vgLt, dt, s->vgpf, s->vgpc,
              s->vgdq, s->vgq0, s->vgQ, s->rs_ptr, s->rs_pos, s->flag, s->st);
   launch_permute_out(nc, s->m.perm, s->vgQ, s->tmp, s->st);

@@ -37,7 +37,19 @@ enum : int {
   kErrInverted = 1,     // a cell Jacobian <= 0 at a quadrature point
   kErrSingular = 2,     // a least-squares system is rank deficient
   kErrNonphysical = 4,  // rho <= 0, p <= 0 or NaN
-  kErrBigStencil = 8
+  kErrBigStencil = 8,
+  kErrTimeout = 16      // a bounded wait on an asynchronous copy ran out
+};
+
+// Contiguous ranges of tiles whose first cell has the same kind (cells are ordered by kind
+// first, so there is one range per kind present). Each range records its largest stencil K, its
+// largest sum S of per-sub-stencil member counts and its largest number M of sub-stencil slots;
+// the reconstruction is launched once per range with shared memory sized for that range.
+constexpr int kMaxTileRanges = 8;
+struct TileRanges {
+  int n = 0;
+  int64_t t0[kMaxTileRanges] = {}, t1[kMaxTileRanges] = {};
+  int K[kMaxTileRanges] = {}, S[kMaxTileRanges] = {}, M[kMaxTileRanges] = {};
 };
 
 // Mesh arrays on the device (internal order).
@@ -67,11 +79,13 @@ struct DevMesh {
   int32_t* t_st = nullptr;
   int32_t* t_sb = nullptr;
   int32_t* t_idx = nullptr;
+  TileRanges rr;
 };
 
 // FP64 geometry (always kept).
 struct Geo64 {
   double* vol = nullptr;     // [nc]
+  double* ivol = nullptr;    // [nc] 1 / |Omega|
   double* cen = nullptr;     // [nc][3]
   double* h = nullptr;       // [nc] |Omega|^(1/3)
   double* mom = nullptr;     // [6][nc] second central moments / (|Omega| h^2): xx yy zz xy xz yz
@@ -113,7 +127,7 @@ void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream
 // ---- hot path (gks_hot.cu) ----------------------------------------------------------------
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
-                  R* poly, cudaStream_t st);
+                  R* poly, int* flag, cudaStream_t st);
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
                  double dt, R* fface, int* flag, cudaStream_t st);

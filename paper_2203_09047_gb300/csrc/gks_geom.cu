@@ -23,7 +23,7 @@ __device__ __forceinline__ double g3w(int i) { return i == 1 ? 4.0 / 9.0 : 5.0 /
 // Per cell: volume, centroid, |Omega|^(1/3), scaled second central moments; flags a cell whose
 // trilinear Jacobian is not positive at every quadrature point.
 __global__ void k_geom_cells(int64_t nc, const double* __restrict__ cell_x, double* vol,
-                             double* cen, double* hh, double* mom, int* flag) {
+                             double* ivol, double* cen, double* hh, double* mom, int* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   double X[8][3];
@@ -74,6 +74,7 @@ __global__ void k_geom_cells(int64_t nc, const double* __restrict__ cell_x, doub
   const double c[3] = {m1[0] / m0, m1[1] / m0, m1[2] / m0};
   const double h = cbrt(m0);
   vol[i] = m0;
+  ivol[i] = 1.0 / m0;
   hh[i] = h;
   for (int a = 0; a < 3; ++a) cen[3 * i + a] = o[a] + c[a];
   // central moments from raw moments about the vertex mean
@@ -319,7 +320,7 @@ void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream
 }
 
 void launch_geom_cells(const DevMesh& m, const Geo64& g, int* flag, cudaStream_t st) {
-  k_geom_cells<<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, m.cell_x, g.vol, g.cen, g.h,
+  k_geom_cells<<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, m.cell_x, g.vol, g.ivol, g.cen, g.h,
                                                                 g.mom, flag);
 }
 template <class R>

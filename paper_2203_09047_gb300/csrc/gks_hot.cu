@@ -84,57 +84,141 @@ __device__ __forceinline__ void stencil_delta(const R* __restrict__ QA, int32_t 
 }
 
 // ------------------------------------------------------------------------------------------
-// Reconstruction, one block of four warps per 32-cell tile (lane = cell). For each conserved
+// Asynchronous bulk copies global -> shared completed on an mbarrier (transaction bytes), and a
+// bounded wait on it.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// bytes: a multiple of 16; dst and src 16-byte aligned
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Each try_wait suspends the thread for at most a hardware time limit; the loop gives up after
+// kWaitTries attempts (far beyond the microseconds a tile's copies take).
+constexpr int kWaitTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kWaitTries; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// Reconstruction, one block of five warps per 32-cell tile (lane = cell). For each conserved
 // variable v of each cell:
 //   dq_k = Q_k - Q_0 over the big stencil                      (phase 1, all warps, to shared)
 //   a    = A+ dq   (quadratic P0, 9 coefficients in centred scaled coordinates) and
 //   b_m  = B_m dq|S_m (linear P_m) with beta_m (Eq. indicator); rows and sub-stencils are
-//   spread over the four warps                                                       (phase 2)
+//   spread over the warps                                                            (phase 2)
 //   beta_0, tau, omega, omega-bar (Section 2), one variable per warp               (phase 3)
 //   C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m, i.e. Eq. weno as one polynomial (phase 4)
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
-// Variables are split over the warps as warp w -> v = w, and warp 0 also takes v = 4.
-constexpr int kReconWarps = 4;
+// With kPf the tile's pseudo-inverse rows and sub-stencil entries (contiguous blocks of the
+// interleaved layouts) are brought into shared memory by two bulk copies issued when the block
+// starts, so that their transfer overlaps phase 1; otherwise phase 2 reads them from global
+// memory.
+constexpr int kReconWarps = 5;
 constexpr int kReconThreads = kReconWarps * kTile;
 
+// Shared-memory layout of one block for a range with largest stencil Kr, largest sum of
+// sub-stencil member counts Sr and largest number of sub-stencil slots Mr, in units of one
+// interleaved row (kTile values): [mbarrier, 16 B][A+ rows 9 Kr][B entries 4 Sr] (only with
+// kPf), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part starts on a 16-byte
+// boundary.
 template <class R>
-struct ReconShared {
-  R a[9][5][kTile];             // big-stencil coefficients
-  R b[kMaxSub][3][5][kTile];    // sub-stencil coefficients
-  R bet[kMaxSub][5][kTile];     // beta_m, then the sub-stencil factors of the combination
-  R ca[5][kTile];               // factor of a in the combination
-  // followed by dq[K][5][kTile]
+struct ReconSmem {
+  size_t a_off, b_off, ca_off, cb_off, cbet_off, dq_off, bytes;
+  __host__ __device__ ReconSmem(int Kr, int Sr, int Mr, bool pf) {
+    const size_t row = (size_t)kTile * sizeof(R);
+    a_off = pf ? 16 : 0;
+    b_off = a_off + (pf ? 9 * (size_t)Kr * row : 0);
+    ca_off = b_off + (pf ? 4 * (size_t)Sr * row : 0);
+    cb_off = ca_off + 45 * row;
+    cbet_off = cb_off + 15 * (size_t)Mr * row;
+    dq_off = cbet_off + 5 * (size_t)Mr * row;
+    bytes = dq_off + 5 * (size_t)Kr * row;
+  }
 };
 
-template <class R>
+template <class R, bool kPf>
 __global__ void __launch_bounds__(kReconThreads) k_recon(
-    int64_t nc, const R* __restrict__ QA, const int32_t* __restrict__ t_K,
-    const uint64_t* __restrict__ t_cnt, const int32_t* __restrict__ t_st,
-    const int32_t* __restrict__ t_sb, const int32_t* __restrict__ t_idx,
-    const int8_t* __restrict__ n_sub, const R* __restrict__ Ap, const R* __restrict__ Bp,
-    const R* __restrict__ mom, const R* __restrict__ hcell, R wg, R weps, int wpow,
-    R* __restrict__ poly) {
+    int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, const R* __restrict__ QA,
+    const int32_t* __restrict__ t_K, const uint64_t* __restrict__ t_cnt,
+    const int32_t* __restrict__ t_st, const int32_t* __restrict__ t_sb,
+    const int32_t* __restrict__ t_idx, const int8_t* __restrict__ n_sub,
+    const R* __restrict__ Ap, const R* __restrict__ Bp, const R* __restrict__ mom,
+    const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly, int* flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  ReconShared<R>& sh = *reinterpret_cast<ReconShared<R>*>(smem_raw);
-  R* sdq = reinterpret_cast<R*>(smem_raw + sizeof(ReconShared<R>));  // [k][v][lane]
-  const int64_t tile = blockIdx.x;
+  const ReconSmem<R> L(Kr, Sr, Mr, kPf);
+  R* sa = reinterpret_cast<R*>(smem_raw + L.ca_off);      // [n][v][lane]
+  R* sb = reinterpret_cast<R*>(smem_raw + L.cb_off);      // [m][t][v][lane]
+  R* sbet = reinterpret_cast<R*>(smem_raw + L.cbet_off);  // [m][v][lane]
+  R* sdq = reinterpret_cast<R*>(smem_raw + L.dq_off);     // [k][v][lane]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
+  const int64_t tile = tile0 + blockIdx.x;
   const int lane = threadIdx.x & (kTile - 1);
   const int warp = threadIdx.x / kTile;
+  const int K = __ldg(t_K + tile);
+  const uint64_t cnt = __ldg(t_cnt + tile);
+  const int64_t st = __ldg(t_st + tile), sbo = __ldg(t_sb + tile);
+  const R* Ag = Ap + st * 9 * kTile;
+  const R* Bg = Bp + sbo * 4 * kTile;
+  int S = 0, Mt = 0;  // entries and sub-stencil slots of this tile
+#pragma unroll
+  for (int q = 0; q < kMaxSub; ++q) {
+    const int c = (int)((cnt >> (8 * q)) & 0xffu);
+    S += c;
+    if (c) Mt = q + 1;
+  }
+  if (kPf) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar);
+      const uint32_t ab = 9u * K * kTile * sizeof(R), bb = 4u * S * kTile * sizeof(R);
+      mbar_expect_tx(bar, ab + bb);
+      bulk_load(smem_raw + L.a_off, Ag, ab, bar);
+      if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
+    }
+  }
   const int64_t i = tile * kTile + lane;
   const bool valid = i < nc;
   const int64_t ic = valid ? i : tile * kTile;  // padded lanes mirror the tile's first cell
-  const int K = __ldg(t_K + tile);
-  const uint64_t cnt = __ldg(t_cnt + tile);
-  const int32_t* sidx = t_idx + (int64_t)__ldg(t_st + tile) * kTile + lane;
-  const R* A = Ap + (int64_t)__ldg(t_st + tile) * 9 * kTile + lane;
-  const R* Bt = Bp + (int64_t)__ldg(t_sb + tile) * 4 * kTile + lane;
+  // per-cell data of the later phases, loaded now so that it arrives during phase 1
+  const int M = n_sub[ic];
+  R m2[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + ic];
+  const R hc = hcell[ic];
+  const int32_t* sidx = t_idx + st * kTile + lane;
   Gq<R> c0;
   c0.load(QA, ic);
+  if (kPf) __syncthreads();  // the barrier is initialised before anyone waits on it
 
-  // phase 1: stencil differences, members split over the warps; the loops below are unrolled
-  // so that several iterations' loads are in flight per warp
+  // phase 1: stencil differences, members split over the warps, four per batch: all index
+  // loads, then all state loads, then the differences
   for (int k0 = warp; k0 < K; k0 += 4 * kReconWarps) {
-    // four members per batch: all index loads, then all state loads, then the differences
     int32_t e[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -157,65 +241,77 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
       for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kTile + lane] = g[u].minus(c0, v);
     }
   }
-  __syncthreads();
+  const R* A;
+  const R* Bt;
+  if (kPf) {
+    // every thread waits for the copies; a block whose wait ran out reports it and stops
+    bool ok = mbar_wait(bar, 0);
+    if (!ok) ok = mbar_wait(bar, 0);  // let copies still in flight land before leaving
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(flag, kErrTimeout);
+      return;
+    }
+    A = reinterpret_cast<const R*>(smem_raw + L.a_off) + lane;
+    Bt = reinterpret_cast<const R*>(smem_raw + L.b_off) + lane;
+  } else {
+    __syncthreads();
+    A = Ag + lane;
+    Bt = Bg + lane;
+  }
 
-  // phase 2, all warps: rows n = warp, warp + 4, warp + 8 of a = A+ dq, and the sub-stencil
-  // fits b_m (m = warp, warp + 4) with their indicators beta_m = |b_m|^2 (scaled coordinates)
+  // phase 2: rows n = warp, warp + 5 of a = A+ dq, and the sub-stencil fits b_m with their
+  // indicators beta_m = |b_m|^2 (scaled coordinates); sub-stencils go to the warps in reverse
+  // order (m = 4 - warp, 9 - warp) so that the warp with one row takes two of them
   for (int n = warp; n < 9; n += kReconWarps) {
     R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-      const R row = __ldg(A + (9 * k + n) * kTile);
+      const R row = kPf ? A[(9 * k + n) * kTile] : __ldg(A + (9 * k + n) * kTile);
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] += row * sdq[(5 * k + v) * kTile + lane];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sh.a[n][v][lane] = acc[v];
+    for (int v = 0; v < 5; ++v) sa[(5 * n + v) * kTile + lane] = acc[v];
   }
-  {
+  for (int s = kReconWarps - 1 - warp; s < Mt; s += kReconWarps) {
     int slot = 0;
-    for (int s = 0; s < warp; ++s) slot += (int)((cnt >> (8 * s)) & 0xffu);
-    for (int s = warp; s < kMaxSub; s += kReconWarps) {
-      const int cs = (int)((cnt >> (8 * s)) & 0xffu);
-      const R* e = Bt + (int64_t)4 * kTile * slot;
-      R b[3][5];
+    for (int q = 0; q < s; ++q) slot += (int)((cnt >> (8 * q)) & 0xffu);
+    const int cs = (int)((cnt >> (8 * s)) & 0xffu);
+    const R* e = Bt + (int64_t)4 * kTile * slot;
+    R b[3][5];
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
+    for (int t = 0; t < 3; ++t)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) b[t][v] = R(0);
+      for (int v = 0; v < 5; ++v) b[t][v] = R(0);
 #pragma unroll 2
-      for (int j = 0; j < cs; ++j, e += 4 * kTile) {
-        const int k = (int)__ldg(e + 3 * kTile);
-        const R c[3] = {__ldg(e), __ldg(e + kTile), __ldg(e + 2 * kTile)};
+    for (int j = 0; j < cs; ++j, e += 4 * kTile) {
+      R c[4];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const R dq = sdq[(5 * k + v) * kTile + lane];
-#pragma unroll
-          for (int t = 0; t < 3; ++t) b[t][v] += c[t] * dq;
-        }
-      }
+      for (int t = 0; t < 4; ++t) c[t] = kPf ? e[t * kTile] : __ldg(e + t * kTile);
+      const int k = (int)c[3];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        sh.bet[s][v][lane] = b[0][v] * b[0][v] + b[1][v] * b[1][v] + b[2][v] * b[2][v];
+        const R dq = sdq[(5 * k + v) * kTile + lane];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) sh.b[s][t][v][lane] = b[t][v];
+        for (int t = 0; t < 3; ++t) b[t][v] += c[t] * dq;
       }
-      // slots of the sub-stencils this warp skips (the other warps' ones)
-      for (int q = s; q < s + kReconWarps && q < kMaxSub; ++q) slot += (int)((cnt >> (8 * q)) & 0xffu);
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sbet[(5 * s + v) * kTile + lane] = b[0][v] * b[0][v] + b[1][v] * b[1][v] + b[2][v] * b[2][v];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) sb[((3 * s + t) * 5 + v) * kTile + lane] = b[t][v];
     }
   }
   __syncthreads();
 
-  // phase 3: nonlinear weights, one variable per warp (warp 0 also does v = 4)
-  const int M = n_sub[ic];
+  // phase 3: nonlinear weights, variable v = warp
   const R g0 = R(1) - wg * R(M);
-  R m2[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + ic];
-  for (int v = warp; v < 5; v += kReconWarps) {
+  const int v = warp;
+  {
     R a[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) a[n] = sh.a[n][v][lane];
+    for (int n = 0; n < 9; ++n) a[n] = sa[(5 * n + v) * kTile + lane];
     // |l| = 1 terms: cell means of the squared first derivatives (linear in the scaled
     // coordinates y, second moments m2); |l| = 2 terms: squared second derivatives
     const R gx[3] = {R(2) * a[3], a[6], a[7]};
@@ -229,7 +325,7 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
                     R(4) * (a[3] * a[3] + a[4] * a[4] + a[5] * a[5]) + a[6] * a[6] + a[7] * a[7] +
                     a[8] * a[8];
     R tau = R(0);
-    for (int s = 0; s < M; ++s) tau += fabs(beta0 - sh.bet[s][v][lane]);
+    for (int s = 0; s < M; ++s) tau += fabs(beta0 - sbet[(5 * s + v) * kTile + lane]);
     tau /= R(M);
     auto weight = [&](R gam, R bb) {
       const R r = tau / (bb + weps);
@@ -239,43 +335,43 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
     };
     const R w0 = weight(g0, beta0);
     R sum = w0;
-    for (int s = 0; s < M; ++s) {
-      const R w = weight(wg, sh.bet[s][v][lane]);
-      sh.bet[s][v][lane] = w;
-      sum += w;
+    R wm[kMaxSub];
+#pragma unroll
+    for (int s = 0; s < kMaxSub; ++s) {
+      wm[s] = s < M ? weight(wg, sbet[(5 * s + v) * kTile + lane]) : R(0);
+      sum += wm[s];
     }
     const R is = R(1) / sum;
     const R wb0 = w0 * is;
     const R corr = wb0 * wg / g0;
-#pragma unroll
-    for (int s = 0; s < kMaxSub; ++s)
-      sh.bet[s][v][lane] = s < M ? sh.bet[s][v][lane] * is - corr : R(0);
-    sh.ca[v][lane] = wb0 / g0;
-  }
-  __syncthreads();
-
-  // phase 4: linear part of the combination and the output, one variable per warp
-  const R ih = R(1) / hcell[ic], ih2 = ih * ih;
-  for (int v = warp; v < 5; v += kReconWarps) {
+    // phase 4 (same warp, same variable): linear part of the combination and the output
     R cl[3] = {R(0), R(0), R(0)};
-    for (int s = 0; s < M; ++s) {
-      const R f = sh.bet[s][v][lane];
 #pragma unroll
-      for (int t = 0; t < 3; ++t) cl[t] += f * sh.b[s][t][v][lane];
+    for (int s = 0; s < kMaxSub; ++s) {
+      if (s < M) {
+        const R f = wm[s] * is - corr;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) cl[t] += f * sb[((3 * s + t) * 5 + v) * kTile + lane];
+      }
     }
-    const R ca = sh.ca[v][lane];
+    const R ca = wb0 / g0;
     R C[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) C[n] = ca * sh.a[n][v][lane];
+    for (int n = 0; n < 9; ++n) C[n] = ca * a[n];
     C[0] += cl[0];
     C[1] += cl[1];
     C[2] += cl[2];
     if (valid) {
+      const R ih = R(1) / hc, ih2 = ih * ih;
       // Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
       const R shift = C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] +
                       C[7] * m2[4] + C[8] * m2[5];
       R* o = poly + (int64_t)kPolyStride * i + 10 * v;
-      o[0] = c0.value_minus(v, shift);
+      R o0 = R(0);  // c0's component v, selected without a dynamic register index
+#pragma unroll
+      for (int q = 0; q < 5; ++q)
+        if (q == v) o0 = c0.value_minus(q, shift);
+      o[0] = o0;
       o[1] = C[0] * ih;
       o[2] = C[1] * ih;
       o[3] = C[2] * ih;
@@ -356,12 +452,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux(
   }
 }
 
-
-template <class R>
-__device__ __forceinline__ bool physical(const double q[5], double gamma) {
-  const double ke = 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / q[0];
-  const double p = (gamma - 1.0) * (q[4] - ke);
-  return q[0] > 0.0 && p > 0.0;
+// rho > 0 and p > 0, the latter as rho E > |m|^2 / 2 (gamma > 1; no division; false for NaN).
+__device__ __forceinline__ bool physical(const double q[5]) {
+  const double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  return q[0] > 0.0 && q[0] * q[4] > 0.5 * m2;
 }
 
 // Sum of the signed face fluxes of one cell (the owner loses the outward flux), in the cell's
@@ -415,14 +509,14 @@ __device__ __forceinline__ void face_sums<float>(int k0, int k1, const int32_t* 
 template <class R>
 __global__ void __launch_bounds__(256) k_gather(
     int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
-    const R* __restrict__ fface, const double* __restrict__ vol, int mode, double dt, double gamma,
+    const R* __restrict__ fface, const double* __restrict__ ivol, int mode, double dt, double gamma,
     double* __restrict__ L, double* __restrict__ Lt, double* __restrict__ Qn,
     double* __restrict__ Qs, R* __restrict__ QA, R* __restrict__ QsA, int* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   double s[10];
   face_sums(cf_ptr[i], cf_ptr[i + 1], cf_idx, fface, s);
-  const double iv = 1.0 / vol[i];
+  const double iv = ivol[i];
   double l[5], lt[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -456,7 +550,7 @@ __global__ void __launch_bounds__(256) k_gather(
     }
     Gq<R>::store(QA, i, q);
   }
-  if (!physical<R>(q, gamma)) atomicOr(flag, kErrNonphysical);
+  if (!physical(q)) atomicOr(flag, kErrNonphysical);
 }
 
 template <class R>
@@ -487,7 +581,7 @@ __global__ void k_check_state(int64_t nc, const double* __restrict__ Q, double g
   double q[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) q[v] = Q[v * nc + i];
-  if (!physical<double>(q, gamma)) atomicOr(flag, kErrNonphysical);
+  if (!physical(q)) atomicOr(flag, kErrNonphysical);
 }
 
 constexpr int kDtThreads = 256;
@@ -534,15 +628,33 @@ __global__ void k_dt_final(const double* partial, int n, double* out) {
 
 }  // namespace
 
+// Largest dynamic shared memory of one block (227 KB on this architecture).
+constexpr size_t kMaxBlockSmem = 227 * 1024;
+
+template <class R, bool kPf>
+void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
+                        R* poly, int* flag, int r, size_t smem, cudaStream_t st) {
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_recon<R, kPf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_recon<R, kPf><<<(unsigned)(m.rr.t1[r] - m.rr.t0[r]), kReconThreads, smem, st>>>(
+      m.nc, m.rr.t0[r], m.rr.K[r], m.rr.S[r], m.rr.M[r], QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
+      m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag);
+}
+
+// One launch per tile range; the bulk-copy variant whenever its shared memory fits a block.
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
-                  R* poly, cudaStream_t st) {
-  const size_t smem = sizeof(ReconShared<R>) + (size_t)m.kmax * 5 * kTile * sizeof(R);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_recon<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_recon<R><<<(unsigned)m.n_tiles, kReconThreads, smem, st>>>(
-      m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb, m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h,
-      p.weno_gamma, p.weno_eps, p.weno_pow, poly);
+                  R* poly, int* flag, cudaStream_t st) {
+  for (int r = 0; r < m.rr.n; ++r) {
+    if (m.rr.t1[r] <= m.rr.t0[r]) continue;
+    const ReconSmem<R> pf(m.rr.K[r], m.rr.S[r], m.rr.M[r], true);
+    if (pf.bytes <= kMaxBlockSmem) {
+      launch_recon_range<R, true>(m, g, p, QA, poly, flag, r, pf.bytes, st);
+    } else {
+      const ReconSmem<R> np(m.rr.K[r], m.rr.S[r], m.rr.M[r], false);
+      launch_recon_range<R, false>(m, g, p, QA, poly, flag, r, np.bytes, st);
+    }
+  }
 }
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
@@ -563,7 +675,7 @@ template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
                    double gamma, double* L, double* Lt, double* Qn, double* Qs, R* QA, R* QsA,
                    int* flag, cudaStream_t st) {
-  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.vol, mode,
+  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.ivol, mode,
                                                        dt, gamma, L, Lt, Qn, Qs, QA, QsA, flag);
 }
 template <class R>
@@ -589,13 +701,13 @@ void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, dou
 }
 
 template void launch_recon<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
-                                   const double*, double*, cudaStream_t);
+                                   const double*, double*, int*, cudaStream_t);
 template void launch_permute_in<double>(int64_t, const int32_t*, const double*, double*, double*,
                                         cudaStream_t);
 template void launch_permute_in<float>(int64_t, const int32_t*, const double*, double*, float*,
                                        cudaStream_t);
 template void launch_recon<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
-                                  const float*, float*, cudaStream_t);
+                                  const float*, float*, int*, cudaStream_t);
 template void launch_flux<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
                                   const double*, double, double*, int*, cudaStream_t);
 template void launch_flux<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
