@@ -393,11 +393,19 @@ struct PolyRef {
 // reconstructions, rotates into the local frame (n1 normal, n2 = n1 x e_k normalised with e_k
 // the axis least aligned with n1, n3 = n1 x n2), computes F^n and dF/dt, rotates back and
 // weights by the quadrature weight; the four are summed with shuffles and written once.
-template <class R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_flux(
+// kFull selects the flux form and kTau0 a zero collision time at compile time, so that each
+// instance carries only the arithmetic (and registers) of its own form.
+#ifndef GKS_FLUX_SMOOTH_MIN_BLOCKS
+#define GKS_FLUX_SMOOTH_MIN_BLOCKS 6  // resident 128-thread blocks per SM, FP32 smooth flux
+#endif
+template <class R, bool kFull, bool kTau0>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS) : 1)
+    k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fgp, const R* __restrict__ poly,
     FluxParams<R> P, R dt, R* __restrict__ fface, int* flag) {
+  P.full = kFull;
+  if (kTau0) P.tau_model = 0;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t f = gid >> 2;
   const bool active = f < nf;
@@ -668,8 +676,11 @@ void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const 
   fp.full = p.flux_mode;
   fp.tau_model = p.tau_model;
   fp.pr_fix = p.pr_fix;
-  k_flux<R><<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall,
-                                                         g.fgp, poly, fp, (R)dt, fface, flag);
+  const unsigned nb = blocks_for(4 * m.nf, 128);
+  auto kern = fp.full ? (fp.tau_model == 0 ? k_flux<R, true, true> : k_flux<R, true, false>)
+                      : (fp.tau_model == 0 ? k_flux<R, false, true> : k_flux<R, false, false>);
+  kern<<<nb, 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly, fp, (R)dt, fface,
+                           flag);
 }
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,

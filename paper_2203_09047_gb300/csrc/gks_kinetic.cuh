@@ -146,6 +146,100 @@ GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
   return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
 }
 
+// Moments of an equilibrium in closed form. For a Maxwellian g(W) of the conserved state W,
+// dg = g (a . psi) with rho <a psi> = dW, so rho <c_d (a psi) psi> is the derivative of the
+// Euler flux along axis d applied to dW. euler_flux_x: rho <u psi> = F_x(W).
+// euler_jvp: A_d(W) dW = dF_d/dW dW, with dU = (dm - U drho)/rho and
+// dp = (gamma - 1) (dE - U . dm + |U|^2 drho / 2).
+template <class R>
+GKS_HD void euler_flux_x(const Prim<R>& w, R E, R F[5]) {
+  const R m = w.rho * w.U;
+  F[0] = m;
+  F[1] = m * w.U + w.p;
+  F[2] = m * w.V;
+  F[3] = m * w.W;
+  F[4] = w.U * (E + w.p);
+}
+template <class R>
+GKS_HD void euler_jvp(const Prim<R>& w, R ir, R gm1, R Ep, int d, const R dq[5], R out[5]) {
+  const R U[3] = {w.U, w.V, w.W};
+  const R du[3] = {(dq[1] - U[0] * dq[0]) * ir, (dq[2] - U[1] * dq[0]) * ir,
+                   (dq[3] - U[2] * dq[0]) * ir};
+  const R u2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+  const R dp = gm1 * (dq[4] - (U[0] * dq[1] + U[1] * dq[2] + U[2] * dq[3]) + R(0.5) * u2 * dq[0]);
+  const R md = w.rho * U[d], dmd = dq[1 + d];
+  out[0] = dmd;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[1 + a] = dmd * U[a] + md * du[a];
+  out[1 + d] += dp;
+  out[4] = du[d] * Ep + U[d] * (dq[4] + dp);  // Ep = E + p
+}
+
+// Half-line equilibrium of one side (u > 0 for s = +1, u < 0 for s = -1) in closed form:
+// A = <1>, A1 = <u>, A2 = <u^2> over the half line, B = exp(-lam U^2) / (2 sqrt(pi lam)) and
+// S = <v^2 + w^2 + xi^2>, so that rho <psi> = rho (A, A1, V A, W A, (A2 + S A) / 2).
+template <class R>
+struct Half {
+  R A, A1, A2, B, S;
+};
+template <class R>
+GKS_HD void half_init(const Prim<R>& w, R K, int s, Half<R>& h) {
+  const R sl = k_sqrt(w.lam);
+  h.A = R(0.5) * k_erfc(-R(s) * sl * w.U);
+  h.B = R(0.28209479177387814) * k_exp(-w.lam * w.U * w.U) / sl;  // 1/(2 sqrt(pi))
+  h.A1 = w.U * h.A + R(s) * h.B;
+  const R hil = R(0.5) / w.lam;
+  h.A2 = w.U * h.A1 + hil * h.A;
+  h.S = w.V * w.V + w.W * w.W + (K + R(2)) * hil;
+}
+template <class R>
+GKS_HD void half_moments(const Prim<R>& w, const Half<R>& h, R Q[5]) {
+  Q[0] = w.rho * h.A;
+  Q[1] = w.rho * h.A1;
+  Q[2] = w.rho * w.V * h.A;
+  Q[3] = w.rho * w.W * h.A;
+  Q[4] = R(0.5) * w.rho * (h.A2 + h.S * h.A);
+}
+// Derivative of rho <psi> (half line) along the conserved increment dq, through the primitive
+// increments dU = (dm - U drho)/rho, dp = (gamma - 1)(dE - U . dm + |U|^2 drho / 2),
+// dlam = lam (drho/rho - dp/p), with dA = s B (2 lam dU + U dlam),
+// dB = -B (2 lam U dU + (U^2 + 1/(2 lam)) dlam). Equals rho <a psi> (half line) for the slope a
+// of the Maxwellian with rho <a psi> = dq over the full line.
+template <class R>
+GKS_HD void half_jvp(const Prim<R>& w, R ir, R gm1, R K, int s, const Half<R>& h, const R dq[5],
+                     R dQ[5]) {
+  const R dU = (dq[1] - w.U * dq[0]) * ir, dV = (dq[2] - w.V * dq[0]) * ir,
+          dW = (dq[3] - w.W * dq[0]) * ir;
+  const R u2 = w.U * w.U + w.V * w.V + w.W * w.W;
+  const R dp = gm1 * (dq[4] - (w.U * dq[1] + w.V * dq[2] + w.W * dq[3]) + R(0.5) * u2 * dq[0]);
+  const R dlam = w.lam * (dq[0] * ir - dp / w.p);
+  const R hil = R(0.5) / w.lam;
+  const R dA = R(s) * h.B * (R(2) * w.lam * dU + w.U * dlam);
+  const R dB = -h.B * (R(2) * w.lam * w.U * dU + (w.U * w.U + hil) * dlam);
+  const R dA1 = dU * h.A + w.U * dA + R(s) * dB;
+  const R dA2 = dU * h.A1 + w.U * dA1 + hil * (dA - h.A * dlam / w.lam);
+  const R dS = R(2) * (w.V * dV + w.W * dW) - (K + R(2)) * hil * dlam / w.lam;
+  dQ[0] = dq[0] * h.A + w.rho * dA;
+  dQ[1] = dq[0] * h.A1 + w.rho * dA1;
+  dQ[2] = dq[0] * w.V * h.A + w.rho * (dV * h.A + w.V * dA);
+  dQ[3] = dq[0] * w.W * h.A + w.rho * (dW * h.A + w.W * dA);
+  dQ[4] = R(0.5) * (dq[0] * (h.A2 + h.S * h.A) + w.rho * (dA2 + dS * h.A + h.S * dA));
+}
+// Moments of the half-line Maxwellian from its closed-form start (orders 0, 1).
+template <class R>
+GKS_HD void half_to_mom(const Prim<R>& w, R K, const Half<R>& h, Mom<R>& M) {
+  const R hil = R(0.5) / w.lam;
+  line_moments<R, 6>(w.V, hil, M.v);
+  line_moments<R, 6>(w.W, hil, M.w);
+  M.u[0] = h.A;
+  M.u[1] = h.A1;
+#pragma unroll
+  for (int n = 2; n < 7; ++n) M.u[n] = w.U * M.u[n - 1] + R(n - 1) * hil * M.u[n - 2];
+  M.xi[0] = R(1);
+  M.xi[1] = K * hil;
+  M.xi[2] = K * (K + R(2)) * hil * hil;
+}
+
 template <class R>
 struct FluxParams {
   R gamma, K, mu, tau_eps, tau_C;
@@ -177,21 +271,91 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   Prim<R> wl, wr, w0;
   bool ok = to_prim(ql, P.gamma, wl) & to_prim(qr, P.gamma, wr);
   if (!ok) return false;
-  Mom<R> Mlp, Mrn;
-  maxwell_moments(wl.U, wl.V, wl.W, wl.lam, P.K, +1, Mlp);
-  maxwell_moments(wr.U, wr.V, wr.W, wr.lam, P.K, -1, Mrn);
+  const R gm1 = P.gamma - R(1);
+  Half<R> hl, hr;
+  half_init(wl, P.K, +1, hl);
+  half_init(wr, P.K, -1, hr);
   // interface equilibrium Q0 from the two half-space moments
   R q0[5], t[5];
-  G(Mlp, 0, 0, 0, 0, q0);
-  G(Mrn, 0, 0, 0, 0, t);
+  half_moments(wl, hl, q0);
+  half_moments(wr, hr, t);
 #pragma unroll
-  for (int q = 0; q < 5; ++q) q0[q] = wl.rho * q0[q] + wr.rho * t[q];
+  for (int q = 0; q < 5; ++q) q0[q] += t[q];
   if (!to_prim(q0, P.gamma, w0)) return false;
-  Mom<R> M0;
-  maxwell_moments(w0.U, w0.V, w0.W, w0.lam, P.K, 0, M0);
-  // slopes of both sides in the three directions
-  R al[3][5], ar[3][5];
+  // conserved-variable slopes of the interface equilibrium, dW_d = rho0 <ab_d psi>_0: the
+  // half-space parts rho <a_d psi>_{u>0} + rho <a_d psi>_{u<0} of both sides' slopes
   const R irl = R(1) / wl.rho, irr = R(1) / wr.rho;
+  R dW[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    half_jvp(wl, irl, gm1, P.K, +1, hl, dql[d], dW[d]);
+    half_jvp(wr, irr, gm1, P.K, -1, hr, dqr[d], t);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) dW[d][q] += t[q];
+  }
+  // equilibrium time slope, rho0 <Ab psi>_0 = -sum_d rho0 <c_d ab_d psi>_0 = -sum_d A_d dW_d,
+  // and the equilibrium flux moments E0 = rho0 <u psi>_0, E2 = rho0 <u Ab psi>_0 = A_x dWt
+  const R ir0 = R(1) / w0.rho, Ep0 = q0[4] + w0.p;
+  R dWt[5], E0[5], E1[5], E2[5];
+  euler_jvp(w0, ir0, gm1, Ep0, 0, dW[0], dWt);
+  euler_jvp(w0, ir0, gm1, Ep0, 1, dW[1], t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dWt[q] += t[q];
+  euler_jvp(w0, ir0, gm1, Ep0, 2, dW[2], t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dWt[q] = -(dWt[q] + t[q]);
+  euler_flux_x(w0, q0[4], E0);
+  euler_jvp(w0, ir0, gm1, Ep0, 0, dWt, E2);
+  R tau = R(0);
+  const R dp = k_abs((wl.p - wr.p) / (wl.p + wr.p));
+  if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
+  if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
+  if (P.tau_model != 0) {
+    // E1 = rho0 <u (ab . c) psi>_0 from the moments of the interface equilibrium
+    Mom<R> M0;
+    maxwell_moments(w0.U, w0.V, w0.W, w0.lam, P.K, 0, M0);
+    R ab[3][5];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      R b[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) b[q] = dW[d][q] * ir0;
+      slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, ab[d]);
+    }
+    Gadotu(M0, ab, 1, E1);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) E1[q] *= w0.rho;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) E1[q] = R(0);  // multiplied by tau = 0 in both flux forms
+  }
+  if (!P.full) {
+    // F(delta) = E0 delta - tau delta (E1 + E2) + delta^2/2 E2: the fit is exact.
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      Fn[q] = E0[q] - tau * (E1[q] + E2[q]);
+      Ft[q] = E2[q];
+    }
+    if (P.pr_fix != R(0)) {
+      // heat flux relative to the interface velocity, from the flux moments F and the conserved
+      // moments m of the time-integrated distribution: m^n = Q0, dm/dt = dWt (the tau terms of
+      // m vanish by the compatibility condition defining Ab)
+      const R u2 = w0.U * w0.U + w0.V * w0.V + w0.W * w0.W;
+      auto heat = [&](const R F[5], const R m[5]) {
+        return F[4] - (w0.U * F[1] + w0.V * F[2] + w0.W * F[3]) + R(0.5) * u2 * F[0] -
+               (w0.U * m[4] - w0.U * (w0.U * m[1] + w0.V * m[2] + w0.W * m[3]) +
+                R(0.5) * w0.U * u2 * m[0]);
+      };
+      const R qn = heat(Fn, q0);
+      const R qt = heat(Ft, dWt);
+      Fn[4] += P.pr_fix * qn;
+      Ft[4] += P.pr_fix * qt;
+    }
+    return true;
+  }
+  // full flux: non-equilibrium parts need both sides' slopes, their time slopes and the
+  // half-space moments
+  R al[3][5], ar[3][5];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R b[5];
@@ -202,66 +366,9 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
     for (int q = 0; q < 5; ++q) b[q] = dqr[d][q] * irr;
     slope_solve(wr.U, wr.V, wr.W, wr.lam, P.K, b, ar[d]);
   }
-  // equilibrium slopes from the half-space moments, and the equilibrium time slope
-  R ab[3][5], Ab[5];
-  const R ir0 = R(1) / w0.rho;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    R sl[5], sr[5], b[5];
-    Ga(Mlp, al[d], 0, 0, 0, sl);
-    Ga(Mrn, ar[d], 0, 0, 0, sr);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = (wl.rho * sl[q] + wr.rho * sr[q]) * ir0;
-    slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, ab[d]);
-  }
-  {
-    R b[5];
-    Gadotu(M0, ab, 0, b);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = -b[q];
-    slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, Ab);
-  }
-  R tau = R(0);
-  const R dp = k_abs((wl.p - wr.p) / (wl.p + wr.p));
-  if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
-  if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
-  // equilibrium flux moments
-  R e0[5], e1[5], e2[5];
-  G(M0, 1, 0, 0, 0, e0);
-  Ga(M0, Ab, 1, 0, 0, e2);
-  if (P.tau_model != 0) {
-    Gadotu(M0, ab, 1, e1);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) e1[q] = R(0);  // multiplied by tau = 0 in both flux forms
-  }
-  if (!P.full) {
-    // F(delta) = rho0 [delta e0 - tau delta (e1 + e2) + delta^2/2 e2]: the fit is exact.
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      Fn[q] = w0.rho * (e0[q] - tau * (e1[q] + e2[q]));
-      Ft[q] = w0.rho * e2[q];
-    }
-    if (P.pr_fix != R(0)) {
-      // heat flux relative to the interface velocity, from the flux moments F and the conserved
-      // moments m of the time-integrated distribution: m^n = Q0, dm/dt = rho0 <A psi>_0
-      // (the tau terms of m vanish by the compatibility condition defining A)
-      R mt[5];
-      Ga(M0, Ab, 0, 0, 0, mt);
-      const R u2 = w0.U * w0.U + w0.V * w0.V + w0.W * w0.W;
-      auto heat = [&](const R F[5], const R m[5], R sc) {
-        return F[4] - (w0.U * F[1] + w0.V * F[2] + w0.W * F[3]) + R(0.5) * u2 * F[0] -
-               sc * (w0.U * m[4] - w0.U * (w0.U * m[1] + w0.V * m[2] + w0.W * m[3]) +
-                     R(0.5) * w0.U * u2 * m[0]);
-      };
-      const R qn = heat(Fn, q0, R(1));
-      const R qt = heat(Ft, mt, w0.rho);
-      Fn[4] += P.pr_fix * qn;
-      Ft[4] += P.pr_fix * qt;
-    }
-    return true;
-  }
-  // full flux: non-equilibrium parts need the time slopes of both sides
+  Mom<R> Mlp, Mrn;
+  half_to_mom(wl, P.K, hl, Mlp);
+  half_to_mom(wr, P.K, hr, Mrn);
   Mom<R> Ml, Mr;
   maxwell_moments(wl.U, wl.V, wl.W, wl.lam, P.K, 0, Ml);
   maxwell_moments(wr.U, wr.V, wr.W, wr.lam, P.K, 0, Mr);
@@ -303,14 +410,14 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   Ga(Mrn, Ar, 1, 0, 0, nr2);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
-    const R geq_n = cn[0] * e0[q] + cn[1] * e1[q] + cn[2] * e2[q];
-    const R geq_t = ct[0] * e0[q] + ct[1] * e1[q] + ct[2] * e2[q];
+    const R geq_n = cn[0] * E0[q] + cn[1] * E1[q] + cn[2] * E2[q];
+    const R geq_t = ct[0] * E0[q] + ct[1] * E1[q] + ct[2] * E2[q];
     const R gl_n = cn[3] * nl0[q] + cn[4] * nl1[q] + cn[5] * nl2[q];
     const R gl_t = ct[3] * nl0[q] + ct[4] * nl1[q] + ct[5] * nl2[q];
     const R gr_n = cn[3] * nr0[q] + cn[4] * nr1[q] + cn[5] * nr2[q];
     const R gr_t = ct[3] * nr0[q] + ct[4] * nr1[q] + ct[5] * nr2[q];
-    Fn[q] = w0.rho * geq_n + wl.rho * gl_n + wr.rho * gr_n;
-    Ft[q] = w0.rho * geq_t + wl.rho * gl_t + wr.rho * gr_t;
+    Fn[q] = geq_n + wl.rho * gl_n + wr.rho * gr_n;
+    Ft[q] = geq_t + wl.rho * gl_t + wr.rho * gr_t;
   }
   return true;
 }

@@ -75,4 +75,8 @@ def test_full_size_free_stream(full):
     S = gks.Solver(mesh, precision=gks.GKS_PREC_MIXED, flux_mode=1, tau_model=1)
     S.set_state(Q)
     S.step(1e-3, 2)
-    assert np.abs(S.get_state().cpu().numpy() - Q).max() < 1e-5
+    # FP32 fluxes: the free-stream residual of a cell is FP32 rounding of its face fluxes,
+    # |dQ| ~ eps32 t |F| A/|Omega|; the largest values sit in the smallest tetrahedra (|Omega|
+    # about 0.4 of the median), the bulk is two orders lower
+    err = np.abs(S.get_state().cpu().numpy() - Q).max(axis=0)
+    assert err.max() < 3e-5 and np.quantile(err, 0.999) < 2e-6
