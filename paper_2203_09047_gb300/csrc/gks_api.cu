@@ -42,10 +42,13 @@ struct gks_solver {
   GeoR<float> gf;
   bool mixed = false;
   // buffers (internal order)
-  double* Q = nullptr;      // state [5][nc]
-  double* Qs = nullptr;     // stage state
-  double* L = nullptr;      // [5][nc]
-  double* Lt = nullptr;
+  // The state lives in the gather copy QA (FP64 values, or float-float pairs on the FP32 path);
+  // Q is its FP64 [5][nc] form, refreshed from QA when a call needs it (q_stale after steps).
+  double* Q = nullptr;      // [5][nc]
+  bool q_stale = false;
+  double* Qs = nullptr;     // staging for the residual calls
+  double* L = nullptr;      // stage-1 L, Lt [5][nc]: 8 bytes per value (FP64, or a float-float
+  double* Lt = nullptr;     // pair on the FP32 path)
   double* tmp = nullptr;    // staging in caller order [5][nc]
   double* tmp2 = nullptr;   // second staging buffer
   void* poly = nullptr;     // [nc][kPolyStride] in R
@@ -142,17 +145,24 @@ KParams<R> kparams(const gks_params& p) {
   return k;
 }
 
+// The precision-R geometry arrays (every field of GeoR<R>).
+template <class R>
+cudaError_t alloc_geo_arrays(gks_solver* s, GeoR<R>& g) {
+  const int64_t nc = s->m.nc, nf = s->m.nf;
+  cudaError_t e;
+  if ((e = salloc(s, &g.Ap, 9 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess) return e;
+  if ((e = salloc(s, &g.Bp, 4 * (int64_t)kTile * s->m.n_tsb)) != cudaSuccess) return e;
+  if ((e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess) return e;
+  if ((e = salloc(s, &g.h, nc)) != cudaSuccess) return e;
+  if ((e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess) return e;
+  return salloc(s, &g.ivol, (sizeof(R) == 4 ? 2 : 1) * nc);
+}
+
 template <class R>
 gks_status alloc_geo(gks_solver* s, GeoR<R>& g) {
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e;
-  if ((e = salloc(s, &g.Ap, 9 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess)
-    return s->cuda_fail(e, "alloc A+");
-  if ((e = salloc(s, &g.Bp, 4 * (int64_t)kTile * s->m.n_tsb)) != cudaSuccess)
-    return s->cuda_fail(e, "alloc B");
-  if ((e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc moments");
-  if ((e = salloc(s, &g.h, nc)) != cudaSuccess) return s->cuda_fail(e, "alloc h");
-  if ((e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face data");
+  if ((e = alloc_geo_arrays(s, g)) != cudaSuccess) return s->cuda_fail(e, "alloc geometry");
   R* poly = nullptr;
   R* ff = nullptr;
   R* qa = nullptr;
@@ -176,10 +186,11 @@ void precompute_r(gks_solver* s, GeoR<R>& g) {
   launch_cast_cells<R>(s->m, s->g, g, s->st);
 }
 
-// One residual evaluation: recon (from the gather copy QinA) -> flux -> gather(mode).
+// One residual evaluation: recon (from the gather copy QinA) -> flux -> face sums: the FP64
+// residual (mode 0) or stage `mode` of the update.
 template <class R>
 void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode, double* L,
-                double* Lt, double* Qn, double* Qs) {
+                double* Lt) {
   const KParams<R> kp = kparams<R>(s->prm);
   int t = s->tick(0);
   launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st);
@@ -188,17 +199,19 @@ void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode
   launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
   s->tock(t);
   t = s->tick(2);
-  launch_gather<R>(s->m, s->g, (const R*)s->fface, mode, dt, s->prm.gamma, L, Lt, Qn, Qs,
-                   (R*)s->QA, (R*)s->QsA, s->flag, s->st);
+  if (mode == 0)
+    launch_gather<R>(s->m, s->g, (const R*)s->fface, L, Lt, s->st);
+  else
+    launch_stage<R>(s->m, g, (const R*)s->fface, mode, dt, L, Lt, (R*)s->QA, (R*)s->QsA,
+                    s->flag, s->st);
   s->tock(t);
 }
 
-void residual_any(gks_solver* s, const void* QinA, double dt, int mode, double* L, double* Lt,
-                  double* Qn, double* Qs) {
+void residual_any(gks_solver* s, const void* QinA, double dt, int mode, double* L, double* Lt) {
   if (s->mixed)
-    residual_r<float>(s, s->gf, QinA, dt, mode, L, Lt, Qn, Qs);
+    residual_r<float>(s, s->gf, QinA, dt, mode, L, Lt);
   else
-    residual_r<double>(s, s->gd, QinA, dt, mode, L, Lt, Qn, Qs);
+    residual_r<double>(s, s->gd, QinA, dt, mode, L, Lt);
 }
 
 // Caller-order state -> internal order (dst) and its gather copy (gq).
@@ -207,6 +220,16 @@ void permute_in_any(gks_solver* s, const double* src, double* dst, void* gq) {
     launch_permute_in<float>(s->m.nc, s->m.perm, src, dst, (float*)gq, s->st);
   else
     launch_permute_in<double>(s->m.nc, s->m.perm, src, dst, (double*)gq, s->st);
+}
+
+// Refresh the FP64 form of the state from its gather copy after steps.
+void sync_q(gks_solver* s) {
+  if (!s->q_stale) return;
+  if (s->mixed)
+    launch_unpack<float>(s->m.nc, (const float*)s->QA, s->Q, s->st);
+  else
+    launch_unpack<double>(s->m.nc, (const double*)s->QA, s->Q, s->st);
+  s->q_stale = false;
 }
 
 gks_status read_flag(gks_solver* s, int* out) {
@@ -441,6 +464,7 @@ gks_status gks_set_state(gks_solver* s, const double* Q) {
   cudaError_t e = cudaMemcpyAsync(s->tmp, Q, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
   if (e != cudaSuccess) return s->cuda_fail(e, "set_state copy");
   permute_in_any(s, s->tmp, s->Q, s->QA);
+  s->q_stale = false;
   e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "set_state");
 }
@@ -448,6 +472,7 @@ gks_status gks_set_state(gks_solver* s, const double* Q) {
 gks_status gks_get_state(gks_solver* s, double* Q) {
   if (!s || !Q) return GKS_E_INVAL;
   const int64_t nc = s->m.nc;
+  sync_q(s);
   launch_permute_out(nc, s->m.perm, s->Q, s->tmp, s->st);
   cudaError_t e = cudaMemcpyAsync(Q, s->tmp, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
   if (e != cudaSuccess) return s->cuda_fail(e, "get_state copy");
@@ -457,6 +482,7 @@ gks_status gks_get_state(gks_solver* s, double* Q) {
 
 gks_status gks_max_dt(gks_solver* s, double cfl, double* dt) {
   if (!s || !dt || !(cfl > 0)) return GKS_E_INVAL;
+  sync_q(s);
   launch_check_state(s->m.nc, s->Q, s->prm.gamma, s->flag, s->st);
   const int nb = dt_blocks(s->m.nc);
   launch_dt(s->m.nc, s->Q, s->g.hdt, s->prm.gamma, s->prm.mu, s->dt_part, nb, s->dt_out, s->st);
@@ -472,10 +498,11 @@ gks_status gks_max_dt(gks_solver* s, double cfl, double* dt) {
 gks_status gks_step(gks_solver* s, double dt, int nsteps) {
   if (!s || !(dt > 0) || nsteps < 0) return GKS_E_INVAL;
   for (int k = 0; k < nsteps; ++k) {
-    // stage 1 on Q^n: L, Lt kept, Qs = Q* ; stage 2 on Q*: Q^{n+1} written into Q
-    residual_any(s, s->QA, dt, 1, s->L, s->Lt, s->Q, s->Qs);
-    residual_any(s, s->QsA, dt, 2, s->L, s->Lt, s->Q, s->Qs);
+    // stage 1 on Q^n (QA): L, Lt kept, Q* to QsA; stage 2 on Q*: Q^{n+1} written into QA
+    residual_any(s, s->QA, dt, 1, s->L, s->Lt);
+    residual_any(s, s->QsA, dt, 2, s->L, s->Lt);
   }
+  if (nsteps > 0) s->q_stale = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
 }
@@ -492,7 +519,7 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
   if (e != cudaSuccess) return s->cuda_fail(e, "residual copy");
   permute_in_any(s, s->tmp, s->Qs, s->QsA);
   launch_check_state(nc, s->Qs, s->prm.gamma, s->flag, s->st);
-  residual_any(s, s->QsA, dt, 0, s->tmp, s->tmp2, nullptr, nullptr);
+  residual_any(s, s->QsA, dt, 0, s->tmp, s->tmp2);
   // tmp, tmp2 hold L, Lt in internal order; write them out in caller order
   launch_permute_out(nc, s->m.perm, s->tmp, s->Qs, s->st);
   e = cudaMemcpyAsync(L, s->Qs, sizeof(double) * 5 * nc, cudaMemcpyDefault, s->st);
@@ -515,11 +542,7 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
     if (s->mixed) {
       // FP64 geometry of its own (the FP32 path keeps only FP32 copies)
       GeoR<double>& g = s->gv;
-      if ((e = salloc(s, &g.Ap, 9 * (int64_t)kTile * s->m.n_tslots)) != cudaSuccess ||
-          (e = salloc(s, &g.Bp, 4 * (int64_t)kTile * s->m.n_tsb)) != cudaSuccess ||
-          (e = salloc(s, &g.mom, 6 * nc)) != cudaSuccess || (e = salloc(s, &g.h, nc)) != cudaSuccess ||
-          (e = salloc(s, &g.fgp, 40 * nf)) != cudaSuccess)
-        return s->cuda_fail(e, "vjp geometry");
+      if ((e = alloc_geo_arrays(s, g)) != cudaSuccess) return s->cuda_fail(e, "vjp geometry");
       precompute_r(s, g);
     } else {
       s->gv = s->gd;
@@ -593,9 +616,10 @@ gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
              4.0 * r * tb + 7.0 * r * nc + kPolyStride * r * nc;
   // flux: face cells and wall flag, Gauss data, polynomials read, face fluxes written
   bytes[1] = 9.0 * nf + 40.0 * r * nf + kPolyStride * r * nc + kFaceStride * r * nf;
-  // face sums + stage update: CSR, face fluxes, volumes, Q^n read, L/Lt and the stage state,
-  // the gather copy of the new state
-  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + kFaceStride * r * nf + 8.0 * nc + 160.0 * nc + 48.0 * nc;
+  // face sums + stage update: CSR, face fluxes, 1/|Omega| (8 B), the state's gather copy read,
+  // L and Lt (written by stage 1, read by stage 2, 8 B per value), the new gather copy written
+  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + kFaceStride * r * nf + 8.0 * nc + 48.0 * nc + 80.0 * nc +
+             48.0 * nc;
   return GKS_OK;
 }
 

@@ -101,6 +101,7 @@ struct GeoR {
   R* mom = nullptr;  // [6][nc]
   R* h = nullptr;    // [nc]
   R* fgp = nullptr;  // [10][4 nf]: dl(3) dr(3) n1(3) w, index 4 f + gauss point
+  R* ivol = nullptr; // 1/|Omega|: [nc] (FP64 path) or [nc][2] float-float pairs (FP32 path)
 };
 
 // Parameters of the hot kernels.
@@ -131,14 +132,19 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
                  double dt, R* fface, int* flag, cudaStream_t st);
-// mode 0: write L, Lt. mode 1: stage 1 (store L, Lt; Qs = Qn + dt/2 L + dt^2/8 Lt).
-// mode 2: stage 2 (Qn += dt L0 + dt^2/6 (Lt0 + 2 Lt)).
-// The stage kernels also write the gather copy of the state they produce (QA for mode 2,
-// QsA for mode 1).
+// Residual output: L = -(1/|Omega|) sum_f s_f F_f and Lt likewise from dF/dt, in FP64.
 template <class R>
-void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
-                   double gamma, double* L, double* Lt, double* Qn, double* Qs, R* QA, R* QsA,
-                   int* flag, cudaStream_t st);
+void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,
+                   cudaStream_t st);
+// One stage of the fourth-order update on the gather copy QA, which holds the state:
+// stage 1 stores L, Lt (FP64 values, or float-float pairs in the same 8 bytes on the FP32 path)
+// and writes Q* to QsA; stage 2 reads them and writes Q^{n+1} to QA.
+template <class R>
+void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage, double dt,
+                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st);
+// The state [5][nc] in FP64 (internal order) from its gather copy.
+template <class R>
+void launch_unpack(int64_t nc, const R* QA, double* Q, cudaStream_t st);
 template <class R>
 void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst, R* gq,
                        cudaStream_t st);

@@ -268,11 +268,18 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
 
 template <class R>
 __global__ void k_cast_cells(int64_t nc, const double* __restrict__ hh, const double* __restrict__ mom,
-                             R* h_out, R* mom_out) {
+                             const double* __restrict__ ivol, R* h_out, R* mom_out, R* ivol_out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   h_out[i] = (R)hh[i];
   for (int k = 0; k < 6; ++k) mom_out[k * nc + i] = (R)mom[k * nc + i];
+  if (sizeof(R) == 4) {  // float-float pair
+    const float hi = (float)ivol[i];
+    ivol_out[2 * i] = (R)hi;
+    ivol_out[2 * i + 1] = (R)(ivol[i] - (double)hi);
+  } else {
+    ivol_out[i] = (R)ivol[i];
+  }
 }
 
 inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -344,7 +351,8 @@ void launch_geom_ls(const DevMesh& m, const Geo64& g, GeoR<R>& gr, int* flag, in
 }
 template <class R>
 void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st) {
-  k_cast_cells<R><<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, g.h, g.mom, gr.h, gr.mom);
+  k_cast_cells<R><<<blocks_for(m.nc, kThreads), kThreads, 0, st>>>(m.nc, g.h, g.mom, g.ivol, gr.h,
+                                                                  gr.mom, gr.ivol);
 }
 
 template void launch_geom_faces<double>(const DevMesh&, const Geo64&, GeoR<double>&, cudaStream_t);

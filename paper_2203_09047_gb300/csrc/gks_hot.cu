@@ -5,8 +5,10 @@
 
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "gks_device.cuh"
+#include "gks_ff.cuh"
 #include "gks_kinetic.cuh"
 
 namespace gks {
@@ -48,6 +50,12 @@ struct Gq<float> {
     p[1] = make_float4(h[4], l[0], l[1], l[2]);
     p[2] = make_float4(l[3], l[4], 0.f, 0.f);
   }
+  __device__ static void store_ff(float* QA, int64_t c, const ff q[5]) {
+    float4* p = reinterpret_cast<float4*>(QA + 12 * c);
+    p[0] = make_float4(q[0].h, q[1].h, q[2].h, q[3].h);
+    p[1] = make_float4(q[4].h, q[0].l, q[1].l, q[2].l);
+    p[2] = make_float4(q[3].l, q[4].l, 0.f, 0.f);
+  }
 };
 template <>
 struct Gq<double> {
@@ -68,6 +76,12 @@ struct Gq<double> {
     p[2] = make_double2(qq[4], 0.0);
   }
 };
+
+// FP64 value of variable v of a gather copy.
+__device__ __forceinline__ double unpack_value(const Gq<float>& g, int v) {
+  return (double)g.hi[v] + (double)g.lo[v];
+}
+__device__ __forceinline__ double unpack_value(const Gq<double>& g, int v) { return g.q[v]; }
 
 // dq[v] = Q_member - Q_0 for one stencil entry (cell | mirrored-axis bits).
 template <class R>
@@ -396,7 +410,7 @@ struct PolyRef {
 // kFull selects the flux form and kTau0 a zero collision time at compile time, so that each
 // instance carries only the arithmetic (and registers) of its own form.
 #ifndef GKS_FLUX_SMOOTH_MIN_BLOCKS
-#define GKS_FLUX_SMOOTH_MIN_BLOCKS 6  // resident 128-thread blocks per SM, FP32 smooth flux
+#define GKS_FLUX_SMOOTH_MIN_BLOCKS 7  // resident 128-thread blocks per SM, FP32 smooth flux
 #endif
 template <class R, bool kFull, bool kTau0>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS) : 1)
@@ -512,53 +526,129 @@ __device__ __forceinline__ void face_sums<float>(int k0, int k1, const int32_t* 
   for (int q = 0; q < 10; ++q) s[q] = (double)hi[q] + (double)lo[q];
 }
 
-// Per cell: L = -(1/|Omega|) sum_f s_f F_f in the cell's fixed face order, then the
-// requested update; the stage kernels also write the gather copy of the state they produce.
+// Per cell: L = -(1/|Omega|) sum_f s_f F_f in the cell's fixed face order, and Lt from dF/dt
+// (the residual of gks_residual), in FP64.
 template <class R>
 __global__ void __launch_bounds__(256) k_gather(
     int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
-    const R* __restrict__ fface, const double* __restrict__ ivol, int mode, double dt, double gamma,
-    double* __restrict__ L, double* __restrict__ Lt, double* __restrict__ Qn,
-    double* __restrict__ Qs, R* __restrict__ QA, R* __restrict__ QsA, int* flag) {
+    const R* __restrict__ fface, const double* __restrict__ ivol, double* __restrict__ L,
+    double* __restrict__ Lt) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   double s[10];
   face_sums(cf_ptr[i], cf_ptr[i + 1], cf_idx, fface, s);
   const double iv = ivol[i];
-  double l[5], lt[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
-    l[v] = s[v] * iv;
-    lt[v] = s[5 + v] * iv;
+    L[v * nc + i] = s[v] * iv;
+    Lt[v * nc + i] = s[5 + v] * iv;
   }
-  if (mode == 0) {
+}
+
+// ------------------------------------------------------------------------------------------
+// The two stages of the fourth-order update (Section 3.3) on the gather copy of the state,
+// which is the solver state itself: FP64 path [q0..q4, 0] per cell; FP32 path the float-float
+// pairs (hi, lo) of each variable. With the cell's face sums s (F^n part) and st (dF/dt part),
+// L = s / |Omega|, Lt = st / |Omega|:
+//   stage 1: keep L, Lt;           Q*      = Q^n + dt/2 L + dt^2/8 Lt
+//   stage 2 (Lt* of Q*):           Q^{n+1} = Q^n + dt L + dt^2/6 (Lt + 2 Lt*)
+// FP32 path: every operation in float-float arithmetic, so the update is conservative to about
+// 2^-46 relative and issues no FP64 instruction.
+
+// Face sums as float-float pairs, components q0..9 (FP32 path).
+__device__ __forceinline__ void face_sums_ff(int k0, int k1, const int32_t* __restrict__ cf_idx,
+                                             const float* __restrict__ fface, int q0, ff s[10]) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      L[v * nc + i] = l[v];
-      Lt[v * nc + i] = lt[v];
+  for (int q = 0; q < 10; ++q) s[q] = ff{0.f, 0.f};
+  for (int k = k0; k < k1; ++k) {
+    const int32_t e = __ldg(cf_idx + k);
+    const float4* fp = reinterpret_cast<const float4*>(fface + (int64_t)kFaceStride * (e >> 1));
+    const float4 a = __ldg(fp), b = __ldg(fp + 1), c = __ldg(fp + 2);
+    const float x[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+    const bool neg = !(e & 1);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      if (q < q0) continue;
+      const ff t = two_sum(s[q].h, neg ? -x[q] : x[q]);
+      s[q] = ff{t.h, __fadd_rn(s[q].l, t.l)};
     }
-    return;
   }
+#pragma unroll
+  for (int q = 0; q < 10; ++q) s[q] = two_sum(s[q].h, s[q].l);
+}
+
+template <bool kSecond>
+__global__ void __launch_bounds__(256) k_stage_f(
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    const float* __restrict__ fface, const ff* __restrict__ ivol, ff c1, ff c2,
+    ff* __restrict__ L, ff* __restrict__ Lt, float* __restrict__ QA, float* __restrict__ QsA,
+    int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  ff s[10];
+  face_sums_ff(cf_ptr[i], cf_ptr[i + 1], cf_idx, fface, kSecond ? 5 : 0, s);
+  const ff iv = ivol[i];
+  Gq<float> g;
+  g.load(QA, i);
+  ff q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const ff qn{g.hi[v], g.lo[v]};
+    const ff lt = ff_mul(s[5 + v], iv);
+    if (!kSecond) {  // c1 = dt/2, c2 = dt^2/8
+      const ff l = ff_mul(s[v], iv);
+      L[v * nc + i] = l;
+      Lt[v * nc + i] = lt;
+      q[v] = ff_add(qn, ff_add(ff_mul(c1, l), ff_mul(c2, lt)));
+    } else {  // c1 = dt, c2 = dt^2/6
+      const ff lt2 = ff_add(Lt[v * nc + i], ff_twice(lt));
+      q[v] = ff_add(qn, ff_add(ff_mul(c1, L[v * nc + i]), ff_mul(c2, lt2)));
+    }
+  }
+  Gq<float>::store_ff(kSecond ? QA : QsA, i, q);
+  // rho > 0 and rho E > |m|^2 / 2 on the leading parts (false for NaN)
+  const float m2 = q[1].h * q[1].h + q[2].h * q[2].h + q[3].h * q[3].h;
+  if (!(q[0].h > 0.f && q[0].h * q[4].h > 0.5f * m2)) atomicOr(flag, kErrNonphysical);
+}
+
+template <bool kSecond>
+__global__ void __launch_bounds__(256) k_stage_d(
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    const double* __restrict__ fface, const double* __restrict__ ivol, double c1, double c2,
+    double* __restrict__ L, double* __restrict__ Lt, double* __restrict__ QA,
+    double* __restrict__ QsA, int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double s[10];
+  face_sums<double>(cf_ptr[i], cf_ptr[i + 1], cf_idx, fface, s);
+  const double iv = ivol[i];
+  Gq<double> g;
+  g.load(QA, i);
   double q[5];
-  if (mode == 1) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      L[v * nc + i] = l[v];
-      Lt[v * nc + i] = lt[v];
-      q[v] = Qn[v * nc + i] + 0.5 * dt * l[v] + (dt * dt / 8.0) * lt[v];
-      Qs[v * nc + i] = q[v];
+  for (int v = 0; v < 5; ++v) {
+    const double lt = s[5 + v] * iv;
+    if (!kSecond) {
+      const double l = s[v] * iv;
+      L[v * nc + i] = l;
+      Lt[v * nc + i] = lt;
+      q[v] = g.q[v] + c1 * l + c2 * lt;
+    } else {
+      q[v] = g.q[v] + c1 * L[v * nc + i] + c2 * (Lt[v * nc + i] + 2.0 * lt);
     }
-    Gq<R>::store(QsA, i, q);
-  } else {
-#pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      q[v] = Qn[v * nc + i] + dt * L[v * nc + i] +
-             (dt * dt / 6.0) * (Lt[v * nc + i] + 2.0 * lt[v]);
-      Qn[v * nc + i] = q[v];
-    }
-    Gq<R>::store(QA, i, q);
   }
+  Gq<double>::store(kSecond ? QA : QsA, i, q);
   if (!physical(q)) atomicOr(flag, kErrNonphysical);
+}
+
+template <class R>
+__global__ void k_unpack(int64_t nc, const R* __restrict__ QA, double* __restrict__ Q) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  Gq<R> g;
+  g.load(QA, i);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Q[v * nc + i] = unpack_value(g, v);
 }
 
 template <class R>
@@ -683,11 +773,41 @@ void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const 
                            flag);
 }
 template <class R>
-void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, int mode, double dt,
-                   double gamma, double* L, double* Lt, double* Qn, double* Qs, R* QA, R* QsA,
-                   int* flag, cudaStream_t st) {
-  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.ivol, mode,
-                                                       dt, gamma, L, Lt, Qn, Qs, QA, QsA, flag);
+void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,
+                   cudaStream_t st) {
+  k_gather<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.ivol, L,
+                                                       Lt);
+}
+template <class R>
+void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage, double dt,
+                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st) {
+  const unsigned nb = blocks_for(m.nc, 256);
+  // stage 1: c1 = dt/2, c2 = dt^2/8; stage 2: c1 = dt, c2 = dt^2/6
+  const double c1 = stage == 1 ? 0.5 * dt : dt, c2 = stage == 1 ? dt * dt / 8.0 : dt * dt / 6.0;
+  if constexpr (std::is_same<R, float>::value) {
+    ff* l = static_cast<ff*>(L);
+    ff* lt = static_cast<ff*>(Lt);
+    const ff* iv = reinterpret_cast<const ff*>(g.ivol);
+    if (stage == 1)
+      k_stage_f<false><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, iv, ff_from(c1),
+                                           ff_from(c2), l, lt, QA, QsA, flag);
+    else
+      k_stage_f<true><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, iv, ff_from(c1),
+                                          ff_from(c2), l, lt, QA, QsA, flag);
+  } else {
+    double* l = static_cast<double*>(L);
+    double* lt = static_cast<double*>(Lt);
+    if (stage == 1)
+      k_stage_d<false><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.ivol, c1, c2, l, lt,
+                                           QA, QsA, flag);
+    else
+      k_stage_d<true><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, g.ivol, c1, c2, l, lt,
+                                          QA, QsA, flag);
+  }
+}
+template <class R>
+void launch_unpack(int64_t nc, const R* QA, double* Q, cudaStream_t st) {
+  k_unpack<R><<<blocks_for(nc, 256), 256, 0, st>>>(nc, QA, Q);
 }
 template <class R>
 void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, double* dst, R* gq,
@@ -723,11 +843,15 @@ template void launch_flux<double>(const DevMesh&, const GeoR<double>&, const KPa
                                   const double*, double, double*, int*, cudaStream_t);
 template void launch_flux<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
                                  const float*, double, float*, int*, cudaStream_t);
-template void launch_gather<double>(const DevMesh&, const Geo64&, const double*, int, double, double,
-                                    double*, double*, double*, double*, double*, double*, int*,
+template void launch_gather<double>(const DevMesh&, const Geo64&, const double*, double*, double*,
                                     cudaStream_t);
-template void launch_gather<float>(const DevMesh&, const Geo64&, const float*, int, double, double,
-                                   double*, double*, double*, double*, float*, float*, int*,
+template void launch_gather<float>(const DevMesh&, const Geo64&, const float*, double*, double*,
                                    cudaStream_t);
+template void launch_stage<double>(const DevMesh&, const GeoR<double>&, const double*, int, double,
+                                   void*, void*, double*, double*, int*, cudaStream_t);
+template void launch_stage<float>(const DevMesh&, const GeoR<float>&, const float*, int, double,
+                                  void*, void*, float*, float*, int*, cudaStream_t);
+template void launch_unpack<double>(int64_t, const double*, double*, cudaStream_t);
+template void launch_unpack<float>(int64_t, const float*, double*, cudaStream_t);
 
 }  // namespace gks
