@@ -116,6 +116,8 @@ def workload_desc(n, nc=None, nf=None):
                         "periodic [0,2]^3, jitter 0.1h seed 1, Euler smooth flux tau=0, CFL 0.5",
             "cells": nc, "faces": nf, "cubes_per_dir": n, "flux": "smooth (Eq. flux-2)",
             "tau": "zero", "cfl": 0.5, "gamma": 1.4,
+            "arithmetic": "FP32; state, face sums and update as float-float pairs (no FP64 "
+                          "instructions); FP64 path reported under fp64",
             "l2": "inputs larger than L2 (geometry and state > 1 GB); no flush"}
 
 
@@ -284,6 +286,11 @@ def run_gpu(args):
     for k, name in enumerate(["recon", "flux", "gather"]):
         kt64[name]["gbs"] = bytes64[k] / (kt64[name]["avg_ms"] * 1e-3) / 1e9
 
+    # DRAM bytes (read + write) per pass from the ncu captures of the FP32 kernels on the
+    # 48^3-cube mesh (profiles/k_recon_float_advection48_ncu.md,
+    # profiles/k_flux_float_smooth_advection48_ncu.md), scaled by cells or faces
+    dram_per_unit = {"recon": (1435.8, nc), "flux": (321.3, nf)}
+
     def roof_for(table, is_mixed):
         dom = max(table, key=lambda k: table[k]["share"] or 0)
         if dom == "flux":
@@ -291,21 +298,26 @@ def run_gpu(args):
             ach = table["flux"]["tflops"]
             return {"kernel": f"k_flux<{'float' if is_mixed else 'double'}>", "bound": "alu",
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None,
+                    "traffic": (dram_per_unit["flux"][0] * dram_per_unit["flux"][1]) if is_mixed else None,
                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM if is_mixed else FP64_LANES_PER_SM}"
                                    f" {'FP32' if is_mixed else 'FP64'} FMA lanes x 2 x {SM_MAX_GHZ} GHz",
                     "flops_per_gauss_point": flops_gp, "special_per_gauss_point": special_gp}
         ach = table[dom]["gbs"]
+        traffic = None
+        if is_mixed and dom in dram_per_unit:
+            traffic = dram_per_unit[dom][0] * dram_per_unit[dom][1]
         return {"kernel": f"k_{dom}", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": None, "peak_source": f"{hbm_src} copy bandwidth"}
+                "frac": ach / hbm, "traffic": traffic, "peak_source": f"{hbm_src} copy bandwidth",
+                "per": "one pass over the mesh (one launch per cell-kind tile range)" if dom == "recon"
+                       else "one launch"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_desc(args.n, nc, nf),
         "clocks": mixed["clocks"],
-        "gpu_launches": int(sum(mixed["kcnt"])),
+        "gpu_launches": int(sum(c * l for c, l in zip(mixed["kcnt"], gks.gks_launches_per_pass(S.h)))),
         "roofline": roof_for(kt, True),
         "kernels": kt,
         "fp64": {"value": v64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64["ms"] / fp64_steps,

@@ -168,10 +168,15 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
 gks_status gks_timing_enable(gks_solver* s, int enable);
 gks_status gks_timing_read(gks_solver* s, double ms[3], int64_t counts[3]);
 
-/* Algorithmic bytes of one launch of each hot kernel (0 reconstruction, 1 face flux,
+/* Algorithmic bytes of one pass of each hot kernel over the mesh (0 reconstruction, 1 face flux,
  * 2 face sum + update as in a two-stage step) for this solver's mesh and precision: every array
  * the kernel must read or write counted once (re-reads through the caches are not counted). */
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]);
+
+/* Kernel launches in one pass of each hot kernel (0 reconstruction: one launch per range of
+ * tiles of one cell kind; 1 face flux; 2 face sum + update), for counting the launches of a
+ * timed region from the pass counts of gks_timing_read. */
+gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]);
 
 /* Algorithmic operation count of one face Gauss point of the flux kernel for a flux mode and
  * collision-time model: *flops counts +, -, *, / (an FMA as two), *special counts exp, erfc and

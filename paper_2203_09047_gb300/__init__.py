@@ -86,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_cell_quadrature.restype = st
     L.gks_kernel_bytes.argtypes = [P, D]
     L.gks_kernel_bytes.restype = st
+    L.gks_launches_per_pass.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    L.gks_launches_per_pass.restype = st
     L.gks_flux_opcount.argtypes = [ctypes.c_int, ctypes.c_int, D, D]
     L.gks_flux_opcount.restype = ctypes.c_int
     L.gks_cfl_dt_noalloc.argtypes = [I64, P, P, ctypes.c_double, ctypes.c_double,
@@ -208,10 +210,17 @@ def gks_cell_quadrature(solver, xq, wq):
 
 
 def gks_kernel_bytes(solver):
-    """Algorithmic bytes per launch of (reconstruction, flux, face sum + update)."""
+    """Algorithmic bytes per pass of (reconstruction, flux, face sum + update)."""
     b = (ctypes.c_double * 3)()
     _check(load_library().gks_kernel_bytes(solver, b), solver)
     return list(b)
+
+
+def gks_launches_per_pass(solver):
+    """Kernel launches in one pass of (reconstruction, flux, face sum + update)."""
+    n = (ctypes.c_int64 * 3)()
+    _check(load_library().gks_launches_per_pass(solver, n), solver)
+    return list(n)
 
 
 def gks_flux_opcount(flux_mode: int, tau_model: int):

@@ -55,6 +55,7 @@ struct gks_solver {
   void* fface = nullptr;    // [nf][kFaceStride] in R
   void* QA = nullptr;       // gather copy of Q (Lay<R>::gq values per cell)
   void* QsA = nullptr;      // gather copy of the stage state
+  ForkJoin fj;             // concurrent reconstruction ranges
   int* flag = nullptr;      // device status bits
   int* bad_cell = nullptr;
   double* dt_part = nullptr;
@@ -193,7 +194,7 @@ void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode
                 double* Lt) {
   const KParams<R> kp = kparams<R>(s->prm);
   int t = s->tick(0);
-  launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st);
+  launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st, &s->fj);
   s->tock(t);
   t = s->tick(1);
   launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
@@ -403,6 +404,18 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
     r.S[r.n - 1] = std::max(r.S[r.n - 1], S);
     r.M[r.n - 1] = std::max(r.M[r.n - 1], M);
   }
+  // auxiliary streams for the concurrent reconstruction ranges (serial if unavailable)
+  if (m.rr.n > 1 && cudaEventCreateWithFlags(&s->fj.fork, cudaEventDisableTiming) == cudaSuccess) {
+    for (int k = 0; k < m.rr.n - 1; ++k) {
+      if (cudaStreamCreateWithFlags(&s->fj.aux[k], cudaStreamNonBlocking) != cudaSuccess) break;
+      if (cudaEventCreateWithFlags(&s->fj.join[k], cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(s->fj.aux[k]);
+        break;
+      }
+      s->fj.n = k + 1;
+    }
+  }
+  cudaGetLastError();  // a failed optional creation leaves no sticky error
   if ((e = supload(s, &s->rs_ptr, h.rs_ptr)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &s->rs_pos, h.rs_pos)) != cudaSuccess) return bad("upload");
   const int64_t nc = m.nc, nf = m.nf;
@@ -623,6 +636,15 @@ gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
   return GKS_OK;
 }
 
+gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]) {
+  if (!s || !launches) return GKS_E_INVAL;
+  launches[0] = 0;
+  for (int r = 0; r < s->m.rr.n; ++r) launches[0] += s->m.rr.t1[r] > s->m.rr.t0[r] ? 1 : 0;
+  launches[1] = 1;
+  launches[2] = 1;
+  return GKS_OK;
+}
+
 gks_status gks_timing_enable(gks_solver* s, int enable) {
   if (!s) return GKS_E_INVAL;
   s->timing = enable != 0;
@@ -664,6 +686,12 @@ void gks_destroy(gks_solver* s) {
     cudaEventDestroy(u.second.second);
   }
   for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+  for (int k = 0; k < s->fj.n; ++k) {
+    cudaStreamSynchronize(s->fj.aux[k]);
+    cudaStreamDestroy(s->fj.aux[k]);
+    cudaEventDestroy(s->fj.join[k]);
+  }
+  if (s->fj.fork) cudaEventDestroy(s->fj.fork);
   if (s->h_dt) cudaFreeHost(s->h_dt);
   delete s;
 }

@@ -126,9 +126,18 @@ void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream
 void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream_t st);
 
 // ---- hot path (gks_hot.cu) ----------------------------------------------------------------
+// Auxiliary streams on which the reconstruction's tile ranges run concurrently with the first
+// one (forked from and joined back into the solver's stream with events).
+struct ForkJoin {
+  int n = 0;  // auxiliary streams available
+  cudaStream_t aux[kMaxTileRanges - 1] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kMaxTileRanges - 1] = {};
+};
+// fj == nullptr: the ranges run one after the other on st.
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
-                  R* poly, int* flag, cudaStream_t st);
+                  R* poly, int* flag, cudaStream_t st, const ForkJoin* fj = nullptr);
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
                  double dt, R* fface, int* flag, cudaStream_t st);

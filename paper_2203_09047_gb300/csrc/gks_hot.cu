@@ -739,18 +739,33 @@ void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p,
       m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag);
 }
 
-// One launch per tile range; the bulk-copy variant whenever its shared memory fits a block.
+// One launch per tile range, the bulk-copy variant whenever its shared memory fits a block. The
+// ranges are independent: with fj, range r > 0 runs on auxiliary stream r - 1, forked from and
+// joined back into st, so that the ranges' blocks share the GPU.
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
-                  R* poly, int* flag, cudaStream_t st) {
+                  R* poly, int* flag, cudaStream_t st, const ForkJoin* fj) {
+  int used = 0;
+  const bool fork = fj && fj->n > 0 && m.rr.n > 1;
+  if (fork) cudaEventRecord(fj->fork, st);
   for (int r = 0; r < m.rr.n; ++r) {
     if (m.rr.t1[r] <= m.rr.t0[r]) continue;
+    cudaStream_t s = st;
+    if (fork && r > 0 && used < fj->n) {
+      s = fj->aux[used];
+      cudaStreamWaitEvent(s, fj->fork, 0);
+    }
     const ReconSmem<R> pf(m.rr.K[r], m.rr.S[r], m.rr.M[r], true);
     if (pf.bytes <= kMaxBlockSmem) {
-      launch_recon_range<R, true>(m, g, p, QA, poly, flag, r, pf.bytes, st);
+      launch_recon_range<R, true>(m, g, p, QA, poly, flag, r, pf.bytes, s);
     } else {
       const ReconSmem<R> np(m.rr.K[r], m.rr.S[r], m.rr.M[r], false);
-      launch_recon_range<R, false>(m, g, p, QA, poly, flag, r, np.bytes, st);
+      launch_recon_range<R, false>(m, g, p, QA, poly, flag, r, np.bytes, s);
+    }
+    if (s != st) {
+      cudaEventRecord(fj->join[used], s);
+      cudaStreamWaitEvent(st, fj->join[used], 0);
+      ++used;
     }
   }
 }
@@ -832,13 +847,13 @@ void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, dou
 }
 
 template void launch_recon<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
-                                   const double*, double*, int*, cudaStream_t);
+                                   const double*, double*, int*, cudaStream_t, const ForkJoin*);
 template void launch_permute_in<double>(int64_t, const int32_t*, const double*, double*, double*,
                                         cudaStream_t);
 template void launch_permute_in<float>(int64_t, const int32_t*, const double*, double*, float*,
                                        cudaStream_t);
 template void launch_recon<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
-                                  const float*, float*, int*, cudaStream_t);
+                                  const float*, float*, int*, cudaStream_t, const ForkJoin*);
 template void launch_flux<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
                                   const double*, double, double*, int*, cudaStream_t);
 template void launch_flux<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
