@@ -175,6 +175,44 @@ GKS_HD void euler_jvp(const Prim<R>& w, R ir, R gm1, R Ep, int d, const R dq[5],
   out[4] = du[d] * Ep + U[d] * (dq[4] + dp);  // Ep = E + p
 }
 
+// Second-moment flux of an equilibrium along axis d, T_d(W) = rho <u c_d psi>, with theta = p/rho:
+//   T_d[0]     = rho (U_0 U_d + theta delta_0d)
+//   T_d[1 + a] = rho (U_0 U_d U_a + theta (U_0 delta_da + U_d delta_0a + U_a delta_0d))
+//   T_d[4]     = rho/2 (U_0 U_d (|U|^2 + (K + 7) theta) + delta_0d theta (|U|^2 + (K + 5) theta))
+// (u = c_0 the normal velocity). second_moment_jvp returns its derivative along the conserved
+// increment dq, which equals rho <u c_d (a psi) psi> for the slope a with rho <a psi> = dq.
+template <class R>
+GKS_HD void second_moment_jvp(const Prim<R>& w, R ir, R gm1, R K, int d, const R dq[5], R out[5]) {
+  const R U[3] = {w.U, w.V, w.W};
+  const R dU[3] = {(dq[1] - U[0] * dq[0]) * ir, (dq[2] - U[1] * dq[0]) * ir,
+                   (dq[3] - U[2] * dq[0]) * ir};
+  const R q = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+  const R dp = gm1 * (dq[4] - (U[0] * dq[1] + U[1] * dq[2] + U[2] * dq[3]) + R(0.5) * q * dq[0]);
+  const R th = w.p * ir;
+  const R dth = (dp - th * dq[0]) * ir;
+  const R dq2 = R(2) * (U[0] * dU[0] + U[1] * dU[1] + U[2] * dU[2]);
+  const R Ud = U[d], dUd = dU[d];
+  const R uu = U[0] * Ud, duu = dU[0] * Ud + U[0] * dUd;  // U_0 U_d and its derivative
+  const R n = d == 0 ? R(1) : R(0);
+  // per unit density: t and its derivative dt; out = drho t + rho dt
+  R t[5], dt[5];
+  t[0] = uu + th * n;
+  dt[0] = duu + dth * n;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R da = a == d ? R(1) : R(0), za = a == 0 ? R(1) : R(0);
+    const R g = U[0] * da + Ud * za + U[a] * n, dg = dU[0] * da + dUd * za + dU[a] * n;
+    t[1 + a] = uu * U[a] + th * g;
+    dt[1 + a] = duu * U[a] + uu * dU[a] + dth * g + th * dg;
+  }
+  const R c7 = K + R(7), c5 = K + R(5);
+  t[4] = R(0.5) * (uu * (q + c7 * th) + n * th * (q + c5 * th));
+  dt[4] = R(0.5) * (duu * (q + c7 * th) + uu * (dq2 + c7 * dth) +
+                    n * (dth * (q + c5 * th) + th * (dq2 + c5 * dth)));
+#pragma unroll
+  for (int k = 0; k < 5; ++k) out[k] = dq[0] * t[k] + w.rho * dt[k];
+}
+
 // Half-line equilibrium of one side (u > 0 for s = +1, u < 0 for s = -1) in closed form:
 // A = <1>, A1 = <u>, A2 = <u^2> over the half line, B = exp(-lam U^2) / (2 sqrt(pi lam)) and
 // S = <v^2 + w^2 + xi^2>, so that rho <psi> = rho (A, A1, V A, W A, (A2 + S A) / 2).
@@ -311,20 +349,14 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
   if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
   if (P.tau_model != 0) {
-    // E1 = rho0 <u (ab . c) psi>_0 from the moments of the interface equilibrium
-    Mom<R> M0;
-    maxwell_moments(w0.U, w0.V, w0.W, w0.lam, P.K, 0, M0);
-    R ab[3][5];
+    // E1 = rho0 <u (ab . c) psi>_0 = sum_d D T_d(W0)[dW_d]
+    second_moment_jvp(w0, ir0, gm1, P.K, 0, dW[0], E1);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      R b[5];
+    for (int d = 1; d < 3; ++d) {
+      second_moment_jvp(w0, ir0, gm1, P.K, d, dW[d], t);
 #pragma unroll
-      for (int q = 0; q < 5; ++q) b[q] = dW[d][q] * ir0;
-      slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, b, ab[d]);
+      for (int q = 0; q < 5; ++q) E1[q] += t[q];
     }
-    Gadotu(M0, ab, 1, E1);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) E1[q] *= w0.rho;
   } else {
 #pragma unroll
     for (int q = 0; q < 5; ++q) E1[q] = R(0);  // multiplied by tau = 0 in both flux forms

@@ -55,6 +55,24 @@ def test_gp_flux_matches_oracle(lib, mode, tau_model):
         np.testing.assert_allclose(F[5:], Ft_o, rtol=0, atol=1e-10 * np.abs(Ft_o).max())
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_gp_flux_large_collision_time_matches_oracle(lib, mode):
+    """mu = 0.2: tau = mu/p + ... makes the tau terms (the second-moment flux of the slopes, E1)
+    a tenth of F^n, so they are pinned to the oracle too."""
+    rng = np.random.default_rng(170 + mode)
+    P = np.array([1.4, 0.2, 0.01, 1.0, mode, 2, 1.0])
+    Po = oracle.params_vec(flux_mode=mode, tau_model=2, mu=0.2)
+    for _ in range(6):
+        ql, qr = _state(rng), _state(rng)
+        dql, dqr = rng.normal(size=(3, 5)) * 0.2, rng.normal(size=(3, 5)) * 0.2
+        dt = 0.01
+        F = _flux(lib, P, np.concatenate([ql, dql.ravel(), qr, dqr.ravel()]), dt)
+        Fo = oracle.gp_flux(Po, ql, dql, qr, dqr, dt)
+        Fn_o, Ft_o = (4 * Fo[0] - Fo[1]) / dt, 4 * (Fo[1] - 2 * Fo[0]) / dt ** 2
+        np.testing.assert_allclose(F[:5], Fn_o, rtol=0, atol=1e-11 * np.abs(Fn_o).max())
+        np.testing.assert_allclose(F[5:], Ft_o, rtol=0, atol=1e-10 * np.abs(Ft_o).max())
+
+
 def test_gp_flux_prandtl_fix_matches_oracle(lib):
     rng = np.random.default_rng(150)
     P = np.array([1.4, 3e-3, 0.01, 1.0, 0, 2, 0.72])
