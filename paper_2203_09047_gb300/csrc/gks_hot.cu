@@ -401,6 +401,26 @@ struct PolyRef {
   const R* __restrict__ p;
   __device__ __forceinline__ R operator()(int v, int j) const { return __ldg(p + 10 * v + j); }
 };
+// A variable's ten coefficients as five pair loads (a cell's record starts on a 16-byte
+// boundary: kPolyStride values of 4 or 8 bytes; variable v at 10 v values).
+__device__ __forceinline__ void load_coefs(const PolyRef<float>& c, int v, float k[10]) {
+  const float2* q = reinterpret_cast<const float2*>(c.p + 10 * v);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float2 t = __ldg(q + i);
+    k[2 * i] = t.x;
+    k[2 * i + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void load_coefs(const PolyRef<double>& c, int v, double k[10]) {
+  const double2* q = reinterpret_cast<const double2*>(c.p + 10 * v);
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const double2 t = __ldg(q + i);
+    k[2 * i] = t.x;
+    k[2 * i + 1] = t.y;
+  }
+}
 
 // ------------------------------------------------------------------------------------------
 // Flux: four consecutive threads per face, one per Gauss point. Each evaluates both sides'

@@ -454,6 +454,14 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   return true;
 }
 
+// The ten coefficients of variable v through the accessor; accessors over device memory
+// provide their own (vector-load) version, found by argument-dependent lookup.
+template <class Coef, class R>
+GKS_HD void load_coefs(const Coef& coef, int v, R k[10]) {
+#pragma unroll
+  for (int j = 0; j < 10; ++j) k[j] = coef(v, j);
+}
+
 // Value and gradient at offset d of a cell polynomial c[v][j] in physical offsets from the
 // centroid: Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz
 // + c9 dydz. `coef(v, j)` returns coefficient j of variable v.
@@ -464,8 +472,7 @@ GKS_HD void eval_poly(const Coef& coef, const R d[3], R val[5], R grad[5][3]) {
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     R k[10];
-#pragma unroll
-    for (int j = 0; j < 10; ++j) k[j] = coef(v, j);
+    load_coefs(coef, v, k);
     val[v] = k[0] + k[1] * d[0] + k[2] * d[1] + k[3] * d[2] + k[4] * xx + k[5] * yy + k[6] * zz +
              k[7] * xy + k[8] * xz + k[9] * yz;
     grad[v][0] = k[1] + R(2) * k[4] * d[0] + k[7] * d[1] + k[8] * d[2];
