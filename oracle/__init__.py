@@ -71,6 +71,7 @@ def lib():
         L.oracle_residual_jvp.argtypes = [P, D, D, D, ctypes.c_double, D, D, D, D]
         L.oracle_residual_cells.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int, I, D, D]
         L.oracle_step.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int]
+        L.oracle_step_implicit.argtypes = [P, D, D, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.oracle_step_jvp.argtypes = [P, D, D, D, ctypes.c_double, ctypes.c_int]
         L.oracle_s2o4_stage1.argtypes = [ctypes.c_int64, D, D, D, ctypes.c_double, D]
         L.oracle_s2o4_stage2.argtypes = [ctypes.c_int64, D, D, D, D, ctypes.c_double, D]
@@ -189,6 +190,14 @@ class Mesh:
     def step(self, params, Q, dt, nsteps=1):
         Q = np.array(Q, dtype=np.float64, order="C", copy=True)
         st = lib().oracle_step(self.h, _d(params), _d(Q), dt, nsteps)
+        if st:
+            raise OracleError(st)
+        return Q
+
+    def step_implicit(self, params, Q, dt, nsteps=1, kmax=3):
+        """Implicit backward-Euler steps, kmax Jacobi iterations each (Section 4)."""
+        Q = np.array(Q, dtype=np.float64, order="C", copy=True)
+        st = lib().oracle_step_implicit(self.h, _d(params), _d(Q), dt, nsteps, kmax)
         if st:
             raise OracleError(st)
         return Q

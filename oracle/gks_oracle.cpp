@@ -28,7 +28,10 @@
 //  * two-stage fourth-order update: Q* = Q + dt/2 L + dt^2/8 Lt,
 //    Q^{n+1} = Q + dt L + dt^2/6 (Lt + 2 Lt*) (Section 3.3, the cited two-stage method);
 //  * reflecting walls: the ghost is the mirror image of the owner; the wall flux has its mass,
-//    energy and tangential-momentum components set to zero.
+//    energy and tangential-momentum components set to zero;
+//  * implicit step (Section 4): the system is written with |Omega_i| (the printed Eq. jacobi
+//    drops the volume of the residual's definition), Res is the GKS residual averaged over the
+//    step, r_f = max over both sides of |U . n| + c at Q^n, S_f n_f the face's area vector.
 
 #include <algorithm>
 #include <array>
@@ -1231,6 +1234,127 @@ int step(const Mesh& m, const Params& P, T* Q, double dt, int nsteps, std::strin
   return ST_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Implicit step (Section 4): backward Euler with the residual's change linearised by the flux
+// splitting F = (T(Q_i) + T(Q_p) - r (Q_p - Q_i))/2 . n S, the resulting system
+//   (|Omega_i|/dt + 1/2 sum_f r_f S_f) dQ_i + 1/2 sum_f [T_n(Q_p + dQ_p) - T_n(Q_p) - r_f dQ_p] S_f
+//     = |Omega_i| Res_i
+// solved by kmax Jacobi iterations from dQ^(0) = |Omega_i| Res_i / D_i. Res_i is the GKS residual
+// averaged over [0, dt]: Res = L + dt/2 Lt (the time integral of the fitted face flux over the
+// step). T_n(Q) = T(Q) . n is the Euler flux through the face with n pointing out of cell i,
+// S_f the face area and r_f = max over the two sides of |U . n| + c at Q^n. A wall face couples
+// the cell to its mirror image.
+double sound_speed_normal(const double* q, const double n[3], double gamma) {
+  const double U[3] = {q[1] / q[0], q[2] / q[0], q[3] / q[0]};
+  const double p = (gamma - 1.0) * (q[4] - 0.5 * q[0] * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
+  return std::fabs(U[0] * n[0] + U[1] * n[1] + U[2] * n[2]) + std::sqrt(gamma * p / q[0]);
+}
+void euler_normal_flux(const double* q, const double n[3], double gamma, double* T) {
+  const double U[3] = {q[1] / q[0], q[2] / q[0], q[3] / q[0]};
+  const double p = (gamma - 1.0) * (q[4] - 0.5 * q[0] * (U[0] * U[0] + U[1] * U[1] + U[2] * U[2]));
+  const double un = U[0] * n[0] + U[1] * n[1] + U[2] * n[2];
+  T[0] = q[0] * un;
+  for (int a = 0; a < 3; ++a) T[1 + a] = q[1 + a] * un + p * n[a];
+  T[4] = (q[4] + p) * un;
+}
+
+int step_implicit(const Mesh& m, const Params& P, double* Q, double dt, int nsteps, int kmax,
+                  std::string& err) {
+  const int n = m.n_cells, nf = (int)m.faces.size();
+  const size_t len = 5 * (size_t)n;
+  // per face: area vector sum_k w_k n_k (out of the owner) and area
+  std::vector<std::array<double, 3>> nrm(nf);
+  std::vector<double> area(nf);
+  for (int f = 0; f < nf; ++f) {
+    double a[3] = {0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) a[c] += m.faces[f].w[k] * m.faces[f].n[k][c];
+    area[f] = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    for (int c = 0; c < 3; ++c) nrm[f][c] = a[c] / area[f];
+  }
+  std::vector<double> L(len), Lt(len), R(len), D(n), dQ(len), dQn(len);
+  auto get = [&](const double* X, int i, double* q) {
+    for (int v = 0; v < 5; ++v) q[v] = X[v * (size_t)n + i];
+  };
+  // the other side of face f seen from cell i: state and increment in cell i's frame, the
+  // unit normal out of cell i
+  auto other = [&](int f, int i, const double* X, const double* dX, double* qp, double* dqp,
+                   double nn[3]) {
+    const Face& fc = m.faces[f];
+    const bool own = fc.owner == i;
+    for (int c = 0; c < 3; ++c) nn[c] = own ? nrm[f][c] : -nrm[f][c];
+    double q[5], dq[5];
+    if (fc.nb < 0) {  // mirror image of the cell
+      get(X, i, q);
+      get(dX, i, dq);
+      transform_state(fc.nb_to_owner, q, qp);
+      transform_state(fc.nb_to_owner, dq, dqp);
+      return;
+    }
+    const int p = own ? fc.nb : fc.owner;
+    get(X, p, q);
+    get(dX, p, dq);
+    // periodic images are translations: the state is the same in both frames
+    for (int v = 0; v < 5; ++v) {
+      qp[v] = q[v];
+      dqp[v] = dq[v];
+    }
+  };
+  for (int s = 0; s < nsteps; ++s) {
+    int st = residual(m, P, Q, dt, L.data(), Lt.data(), err);
+    if (st) return st;
+    for (int i = 0; i < n; ++i) {
+      double sum = 0.0, qi[5];
+      get(Q, i, qi);
+      for (int f : m.cells[i].face_id) {
+        double qp[5], dqp[5], nn[3];
+        other(f, i, Q, Q, qp, dqp, nn);
+        const double r = std::max(sound_speed_normal(qi, nn, P.gamma),
+                                  sound_speed_normal(qp, nn, P.gamma));
+        sum += 0.5 * r * area[f];
+      }
+      D[i] = m.cells[i].vol / dt + sum;
+      for (int v = 0; v < 5; ++v) {
+        const size_t k = v * (size_t)n + i;
+        R[k] = m.cells[i].vol * (L[k] + 0.5 * dt * Lt[k]);
+        dQ[k] = R[k] / D[i];
+      }
+    }
+    for (int it = 0; it < kmax; ++it) {
+      for (int i = 0; i < n; ++i) {
+        double acc[5] = {0, 0, 0, 0, 0}, qi[5];
+        get(Q, i, qi);
+        for (int f : m.cells[i].face_id) {
+          double qp[5], dqp[5], nn[3], q1[5], T0[5], T1[5];
+          other(f, i, Q, dQ.data(), qp, dqp, nn);
+          const double r = std::max(sound_speed_normal(qi, nn, P.gamma),
+                                    sound_speed_normal(qp, nn, P.gamma));
+          for (int v = 0; v < 5; ++v) q1[v] = qp[v] + dqp[v];
+          euler_normal_flux(q1, nn, P.gamma, T1);
+          euler_normal_flux(qp, nn, P.gamma, T0);
+          for (int v = 0; v < 5; ++v) acc[v] += 0.5 * (T1[v] - T0[v] - r * dqp[v]) * area[f];
+        }
+        for (int v = 0; v < 5; ++v) {
+          const size_t k = v * (size_t)n + i;
+          dQn[k] = (R[k] - acc[v]) / D[i];
+        }
+      }
+      std::swap(dQ, dQn);
+    }
+    for (size_t k = 0; k < len; ++k) Q[k] += dQ[k];
+    for (int i = 0; i < n; ++i) {
+      double q[5];
+      Prim<double> w;
+      get(Q, i, q);
+      if (!primitive(q, P.gamma, w)) {
+        err = "non-physical state after the implicit update in cell " + std::to_string(i);
+        return ST_NONPHYS;
+      }
+    }
+  }
+  return ST_OK;
+}
+
 }  // namespace
 
 // =============================================================================================
@@ -1487,6 +1611,14 @@ int oracle_step(void* h, const double* params, double* Q, double dt, int nsteps)
   Mesh* m = static_cast<Mesh*>(h);
   std::string err;
   return step(*m, read_params(params), Q, dt, nsteps, err);
+}
+
+// Implicit backward-Euler steps with kmax Jacobi iterations (Section 4).
+int oracle_step_implicit(void* h, const double* params, double* Q, double dt, int nsteps,
+                         int kmax) {
+  Mesh* m = static_cast<Mesh*>(h);
+  std::string err;
+  return step_implicit(*m, read_params(params), Q, dt, nsteps, kmax, err);
 }
 
 // S2O4 with a forward tangent: Q and dQ are advanced together.
