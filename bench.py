@@ -45,6 +45,8 @@ def parse():
                     help="timed steps of the FP64 path (default: steps // 4, at least 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-implicit", action="store_true",
+                    help="skip the implicit (Jacobi) workloads reported beside the headline")
     return ap.parse_args()
 
 
@@ -179,6 +181,56 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+IMPLICIT_CASES = [
+    # name, cubes, layers box, bc, params, paper (cells, ms per step) for context
+    ("cavity_like", 32, ((0, 0, 0), (1, 1, 1)), (1, 1, 1),
+     dict(flux_mode=0, tau_model=2, mu=1e-3), (102400, 97.0)),
+    ("sphere_like", 48, ((0, 0, 0), (2, 2, 2)), (0, 0, 0),
+     dict(flux_mode=1, tau_model=1), (462673, 1093.0)),
+]
+
+
+def run_implicit(gks, I, stream, torch, kmax=3, steps=10, warmup=3):
+    """ms per implicit step (one residual + kmax Jacobi sweeps) for FP64 and mixed precision."""
+    out = {}
+    for name, n, (lo, hi), bc, params, (p_cells, p_ms) in IMPLICIT_CASES:
+        m = I.layered_box_mesh(n, "hybrid8", lo=lo, hi=hi, bc=bc)
+        mesh = gks.Mesh(m)
+        if bc[0] == 1:  # gas at rest with a smooth perturbation in the walled box
+            rest = np.tile(np.array([1.0, 0.0, 0.0, 0.0, 2.5])[:, None], (1, mesh.n_cells))
+            Q0 = I.perturbed_state(rest, seed=7, amp=0.02)
+        else:
+            Q0 = I.advection_state(m)
+        rec = {"cells": mesh.n_cells, "faces": mesh.n_faces, "kmax": kmax,
+               "flux": "smooth" if params["flux_mode"] == 0 else "full",
+               "tau": ["zero", "inviscid", "viscous"][params["tau_model"]],
+               "bc": "reflecting walls" if bc[0] == 1 else "periodic",
+               "paper": {"cells": p_cells, "ms_per_step": p_ms, "hardware": "TITAN RTX, FP64",
+                         "cell_steps_per_s": p_cells * 1e3 / p_ms}}
+        for prec, key in ((gks.GKS_PREC_FP64, "fp64"), (gks.GKS_PREC_MIXED, "mixed")):
+            S = gks.Solver(mesh, stream=stream, precision=prec, **params)
+            S.set_state(Q0)
+            dt = S.max_dt(2.0)
+            for _ in range(warmup):
+                S.step_implicit(dt, 1, kmax, check=False)
+            gks.gks_check(S.h)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            gks.gks_step_implicit(S.h, dt, steps, kmax)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            gks.gks_check(S.h)
+            ms = ev0.elapsed_time(ev1) / steps
+            lpp = gks.gks_launches_per_pass(S.h)
+            rec[key] = {"ms_per_step": ms, "cell_steps_per_s": mesh.n_cells / (ms * 1e-3),
+                        "steps": steps, "warmup": warmup, "cfl": 2.0,
+                        "gpu_launches_per_step": lpp[0] + lpp[1] + 1 + kmax}
+            S.close()
+        out[name] = rec
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -346,6 +398,11 @@ def run_gpu(args):
         line["e2e"] = {"value": nc * 2 * e_steps / el, "unit": UNIT, "steps": e_steps,
                        "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Qo.numel() * 8),
                        "api": "gks_set_state(host) + gks_step + gks_get_state(host)"}
+
+    # the implicit Jacobi path (Section 4) on workloads sized like the paper's two timed cases,
+    # reported beside the headline with the paper's own times (TITAN RTX, FP64) as context
+    if not args.no_implicit:
+        line["implicit"] = run_implicit(gks, I, stream, torch)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         import oracle

@@ -140,6 +140,20 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps);
  * rho <= 0, p <= 0 or NaN (the device flag is then cleared). */
 gks_status gks_check(gks_solver* s);
 
+/* nsteps implicit steps for steady problems (Section 4, Jacobi iteration): per step the
+ * residual averaged over [0, dt], |Omega_i| Res_i = -sum_f s_f int_0^dt F_f dt / dt (the
+ * reconstruction and flux of gks_step), then the backward-Euler system with the residual's
+ * change linearised by the flux splitting (T(Q_i) + T(Q_p) - r_f (Q_p - Q_i))/2 . n S:
+ *   (|Omega_i|/dt + 1/2 sum_f r_f S_f) dQ_i + 1/2 sum_f [T_n(Q_p + dQ_p) - T_n(Q_p) - r_f dQ_p] S_f
+ *     = |Omega_i| Res_i,
+ * solved by kmax >= 1 Jacobi iterations from dQ^(0) = |Omega_i| Res_i / D_i, and
+ * Q^{n+1} = Q^n + dQ^(kmax). T_n is the Euler flux through the face (n out of cell i, S the
+ * face area), r_f = max over both sides of |U . n| + c at Q^n; a wall face couples a cell to
+ * its mirror image. The first call allocates the step's buffers (face normals, residual,
+ * diagonal, two iterates). Errors: GKS_E_INVAL (dt <= 0, nsteps < 0, kmax < 1), GKS_E_NOMEM,
+ * GKS_E_CUDA; non-physical states are reported by gks_check. */
+gks_status gks_step_implicit(gks_solver* s, double dt, int nsteps, int kmax);
+
 /* Evaluate L(Q) and its time derivative Lt for a given state Q (Eq. finite):
  *   L_i  = -(1/|Omega_i|) sum_f s_if F_f^n,   Lt_i = -(1/|Omega_i|) sum_f s_if dF_f/dt,
  * F^n = (4 F(dt/2) - F(dt))/dt and dF/dt = 4 (F(dt) - 2 F(dt/2))/dt^2 from the time integrals

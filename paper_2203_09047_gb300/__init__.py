@@ -72,6 +72,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_max_dt.restype = st
     L.gks_step.argtypes = [P, ctypes.c_double, ctypes.c_int]
     L.gks_step.restype = st
+    L.gks_step_implicit.argtypes = [P, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    L.gks_step_implicit.restype = st
     L.gks_check.argtypes = [P]
     L.gks_check.restype = st
     L.gks_residual.argtypes = [P, P, ctypes.c_double, P, P]
@@ -178,6 +180,10 @@ def gks_max_dt(solver, cfl: float) -> float:
 
 def gks_step(solver, dt: float, nsteps: int = 1):
     _check(load_library().gks_step(solver, dt, nsteps), solver)
+
+
+def gks_step_implicit(solver, dt: float, nsteps: int = 1, kmax: int = 3):
+    _check(load_library().gks_step_implicit(solver, dt, nsteps, kmax), solver)
 
 
 def gks_check(solver):
@@ -321,6 +327,12 @@ class Solver:
 
     def step(self, dt: float, nsteps: int = 1, check: bool = True):
         gks_step(self.h, dt, nsteps)
+        if check:
+            gks_check(self.h)
+
+    def step_implicit(self, dt: float, nsteps: int = 1, kmax: int = 3, check: bool = True):
+        """Implicit backward-Euler steps with kmax Jacobi iterations (Section 4)."""
+        gks_step_implicit(self.h, dt, nsteps, kmax)
         if check:
             gks_check(self.h)
 

@@ -56,6 +56,13 @@ struct gks_solver {
   void* QA = nullptr;       // gather copy of Q (Lay<R>::gq values per cell)
   void* QsA = nullptr;      // gather copy of the stage state
   ForkJoin fj;             // concurrent reconstruction ranges
+  // implicit step (allocated on the first gks_step_implicit call), precision R:
+  bool imp_ready = false;
+  void* jfn = nullptr;      // [nf][4] unit normal out of the owner, area
+  void* jR = nullptr;       // [5][nc] |Omega| Res
+  void* jD = nullptr;       // [nc] Jacobi diagonal
+  void* jhrs = nullptr;     // [cf entries] r_f S_f / 2
+  void* jdQ[2] = {nullptr, nullptr};  // [5][nc] Jacobi iterates
   int* flag = nullptr;      // device status bits
   int* bad_cell = nullptr;
   double* dt_part = nullptr;
@@ -274,6 +281,50 @@ bool valid_params(const gks_params* p, std::string& why) {
   return true;
 }
 
+template <class R>
+gks_status step_implicit_r(gks_solver* s, GeoR<R>& g, double dt, int nsteps, int kmax) {
+  const int64_t nc = s->m.nc, nf = s->m.nf;
+  cudaError_t e = cudaSuccess;
+  if (!s->imp_ready) {
+    R *fn = nullptr, *rv = nullptr, *d = nullptr, *hrs = nullptr, *a = nullptr, *b = nullptr;
+    if ((e = salloc(s, &fn, 4 * nf)) != cudaSuccess || (e = salloc(s, &rv, 5 * nc)) != cudaSuccess ||
+        (e = salloc(s, &d, nc)) != cudaSuccess || (e = salloc(s, &hrs, s->m.ncf)) != cudaSuccess ||
+        (e = salloc(s, &a, 5 * nc)) != cudaSuccess || (e = salloc(s, &b, 5 * nc)) != cudaSuccess)
+      return s->cuda_fail(e, "implicit buffers");
+    s->jfn = fn;
+    s->jR = rv;
+    s->jD = d;
+    s->jhrs = hrs;
+    s->jdQ[0] = a;
+    s->jdQ[1] = b;
+    launch_face_normals<R>(s->m, fn, s->st);
+    s->imp_ready = true;
+  }
+  const KParams<R> kp = kparams<R>(s->prm);
+  R* dq[2] = {(R*)s->jdQ[0], (R*)s->jdQ[1]};
+  for (int n = 0; n < nsteps; ++n) {
+    int t = s->tick(0);
+    launch_recon<R>(s->m, g, kp, (const R*)s->QA, (R*)s->poly, s->flag, s->st, &s->fj);
+    s->tock(t);
+    t = s->tick(1);
+    launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
+    s->tock(t);
+    t = s->tick(2);
+    launch_jacobi_init<R>(s->m, (const R*)s->fface, (const R*)s->jfn, s->g.vol, dt,
+                          (const R*)s->QA, (R*)s->jR, (R*)s->jD, (R*)s->jhrs, dq[0],
+                          s->prm.gamma, s->st);
+    for (int it = 1; it <= kmax; ++it)
+      launch_jacobi_sweep<R>(s->m, (const R*)s->jfn, (const R*)s->QA, (const R*)s->jR,
+                             (const R*)s->jD, (const R*)s->jhrs, dq[(it - 1) & 1], dq[it & 1],
+                             it == kmax, (R*)s->QsA, s->prm.gamma, s->flag, s->st);
+    s->tock(t);
+    std::swap(s->QA, s->QsA);  // Q^{n+1} was written to the other gather copy
+  }
+  if (nsteps > 0) s->q_stale = true;
+  e = cudaGetLastError();
+  return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "implicit step launch");
+}
+
 }  // namespace
 
 extern "C" {
@@ -367,6 +418,7 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.f_shift, h.f_shift)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.cf_ptr, h.cf_ptr)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.cf_idx, h.cf_idx)) != cudaSuccess) return bad("upload");
+  m.ncf = (int64_t)h.cf_idx.size();
   if ((e = supload(s, &m.st_ptr, h.st_ptr)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.st_idx, h.st_idx)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.st_xf, h.st_xf)) != cudaSuccess) return bad("upload");
@@ -518,6 +570,12 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps) {
   if (nsteps > 0) s->q_stale = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
+}
+
+gks_status gks_step_implicit(gks_solver* s, double dt, int nsteps, int kmax) {
+  if (!s || !(dt > 0) || nsteps < 0 || kmax < 1) return GKS_E_INVAL;
+  return s->mixed ? step_implicit_r<float>(s, s->gf, dt, nsteps, kmax)
+                  : step_implicit_r<double>(s, s->gd, dt, nsteps, kmax);
 }
 
 gks_status gks_check(gks_solver* s) {

@@ -66,6 +66,7 @@ struct DevMesh {
   double* f_shift = nullptr;  // [nf][3]
   int32_t* cf_ptr = nullptr;
   int32_t* cf_idx = nullptr;
+  int64_t ncf = 0;  // cell-face entries
   int32_t* st_ptr = nullptr;
   int32_t* st_idx = nullptr;
   double* st_xf = nullptr;    // [nst][6]
@@ -124,6 +125,9 @@ void launch_geom_ls(const DevMesh& m, const Geo64& g, GeoR<R>& gr, int* flag, in
 template <class R>
 void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream_t st);
 void launch_cell_quadrature(const DevMesh& m, double* xq, double* wq, cudaStream_t st);
+// Unit normal out of the owner and area of every face, [nf][4] in precision R.
+template <class R>
+void launch_face_normals(const DevMesh& m, R* out, cudaStream_t st);
 
 // ---- hot path (gks_hot.cu) ----------------------------------------------------------------
 // Auxiliary streams on which the reconstruction's tile ranges run concurrently with the first
@@ -151,6 +155,21 @@ void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, 
 template <class R>
 void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage, double dt,
                   void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st);
+// Implicit step (Section 4) on the gather copy QA (the state), after the reconstruction and
+// flux of Q^n: jacobi_init forms |Omega| Res = s + dt/2 st from the face sums, the diagonal
+// D = |Omega|/dt + 1/2 sum_f r_f S_f, the per-entry factors hrs = 1/2 r_f S_f (cell-face CSR
+// order) and dQ0 = |Omega| Res / D; each jacobi_sweep forms dQ^(k) from dQ^(k-1), the last one
+// (last != 0) writes Q^n + dQ to QAout (the other gather copy) in place of dQ. Buffers are in precision R: Rv, dQ
+// [5][nc], D [nc], hrs [cf entries]; fn is [nf][4] from launch_face_normals.
+template <class R>
+void launch_jacobi_init(const DevMesh& m, const R* fface, const R* fn, const double* vol,
+                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0, double gamma,
+                        cudaStream_t st);
+template <class R>
+void launch_jacobi_sweep(const DevMesh& m, const R* fn, const R* QA, const R* Rv, const R* D,
+                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout, double gamma,
+                         int* flag, cudaStream_t st);
+
 // The state [5][nc] in FP64 (internal order) from its gather copy.
 template <class R>
 void launch_unpack(int64_t nc, const R* QA, double* Q, cudaStream_t st);

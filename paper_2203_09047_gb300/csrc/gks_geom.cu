@@ -355,6 +355,32 @@ void launch_cast_cells(const DevMesh& m, const Geo64& g, GeoR<R>& gr, cudaStream
                                                                   gr.mom, gr.ivol);
 }
 
+// Unit normal (out of the owner) and area of every face, [nf][4] = (n, S), from its area vector
+// int X_eta x X_zeta over [-1/2,1/2]^2 = 1/2 (v4 - v2) x (v3 - v1) for the cyclic vertex list
+// v1..v4 (exact for the bilinear face: the integrand is bilinear, its mean is its centre value).
+template <class R>
+__global__ void k_face_normals(int64_t nf, const double* __restrict__ f_vert, R* out) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const double* v = f_vert + 12 * f;
+  double a[3], b[3];
+  for (int c = 0; c < 3; ++c) {
+    a[c] = v[9 + c] - v[3 + c];  // v4 - v2
+    b[c] = v[6 + c] - v[c];      // v3 - v1
+  }
+  const double S[3] = {0.5 * (a[1] * b[2] - a[2] * b[1]), 0.5 * (a[2] * b[0] - a[0] * b[2]),
+                       0.5 * (a[0] * b[1] - a[1] * b[0])};
+  const double area = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+  for (int c = 0; c < 3; ++c) out[4 * f + c] = (R)(S[c] / area);
+  out[4 * f + 3] = (R)area;
+}
+template <class R>
+void launch_face_normals(const DevMesh& m, R* out, cudaStream_t st) {
+  k_face_normals<R><<<blocks_for(m.nf, kThreads), kThreads, 0, st>>>(m.nf, m.f_vert, out);
+}
+template void launch_face_normals<double>(const DevMesh&, double*, cudaStream_t);
+template void launch_face_normals<float>(const DevMesh&, float*, cudaStream_t);
+
 template void launch_geom_faces<double>(const DevMesh&, const Geo64&, GeoR<double>&, cudaStream_t);
 template void launch_geom_faces<float>(const DevMesh&, const Geo64&, GeoR<float>&, cudaStream_t);
 template void launch_geom_ls<double>(const DevMesh&, const Geo64&, GeoR<double>&, int*, int*,

@@ -661,6 +661,190 @@ __global__ void __launch_bounds__(256) k_stage_d(
   if (!physical(q)) atomicOr(flag, kErrNonphysical);
 }
 
+// ------------------------------------------------------------------------------------------
+// Implicit step (Section 4): backward Euler with the residual's change linearised by the flux
+// splitting (T(Q_i) + T(Q_p) - r (Q_p - Q_i))/2 . n S, solved by Jacobi iterations:
+//   (|Omega_i|/dt + 1/2 sum_f r_f S_f) dQ_i^(k)
+//     = |Omega_i| Res_i - 1/2 sum_f [T_n(Q_p + dQ_p^(k-1)) - T_n(Q_p) - r_f dQ_p^(k-1)] S_f,
+// |Omega_i| Res_i = s + dt/2 st (the face sums of F^n and dF/dt: the step-averaged GKS flux),
+// r_f = max over the two sides of |U . n| + c at Q^n, n out of cell i; a wall face couples the
+// cell to its mirror image. The Euler-flux change is formed from the increments themselves
+// (du = (dm - u drho)/rho', dp = (gamma - 1)(dE - (m . du + dm . u')/2)), so no two nearly equal
+// fluxes are subtracted.
+
+template <class R>
+__device__ __forceinline__ void state_of(const R* __restrict__ QA, int64_t c, R q[5]) {
+  Gq<R> g;
+  g.load(QA, c);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v] = (R)g.value(v);
+}
+template <class R>
+__device__ __forceinline__ R wave_speed(const R q[5], const R n[3], R gm1) {
+  const R ir = R(1) / q[0];
+  const R u[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const R p = gm1 * (q[4] - R(0.5) * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  const R c2 = (gm1 + R(1)) * p * ir;
+  return fabs(u[0] * n[0] + u[1] * n[1] + u[2] * n[2]) + sqrt(c2 > R(0) ? c2 : R(0));
+}
+template <class R>
+__device__ __forceinline__ void euler_flux_change(const R q[5], const R d[5], const R n[3], R gm1,
+                                                  R out[5]) {
+  const R ir = R(1) / q[0], ir1 = R(1) / (q[0] + d[0]);
+  R u[3], du[3], u1[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u[a] = q[1 + a] * ir;
+    du[a] = (d[1 + a] - u[a] * d[0]) * ir1;
+    u1[a] = u[a] + du[a];
+  }
+  const R un = u[0] * n[0] + u[1] * n[1] + u[2] * n[2];
+  const R dun = du[0] * n[0] + du[1] * n[1] + du[2] * n[2], un1 = un + dun;
+  const R p = gm1 * (q[4] - R(0.5) * (q[1] * u[0] + q[2] * u[1] + q[3] * u[2]));
+  const R dp = gm1 * (d[4] - R(0.5) * (q[1] * du[0] + q[2] * du[1] + q[3] * du[2] +
+                                       d[1] * u1[0] + d[2] * u1[1] + d[3] * u1[2]));
+  out[0] = d[1] * n[0] + d[2] * n[1] + d[3] * n[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[1 + a] = d[1 + a] * un1 + q[1 + a] * dun + dp * n[a];
+  out[4] = (d[4] + dp) * un1 + (q[4] + p) * dun;
+}
+
+// The other side of cell-face entry e seen from cell i: its index (-1: mirror image across wall
+// axis *wall) and the unit normal out of cell i with the face area.
+template <class R>
+__device__ __forceinline__ int64_t other_side(int32_t e, const int32_t* __restrict__ f_owner,
+                                              const int32_t* __restrict__ f_nb,
+                                              const int8_t* __restrict__ f_wall,
+                                              const R* __restrict__ fn, R n[3], R& S, int& wall) {
+  const int64_t f = e >> 1;
+  const bool nbside = e & 1;
+  const R sg = nbside ? R(-1) : R(1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) n[a] = sg * fn[4 * f + a];
+  S = fn[4 * f + 3];
+  const int64_t p = nbside ? f_owner[f] : f_nb[f];
+  wall = p < 0 ? f_wall[f] : -1;
+  return p;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_jacobi_init(
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
+    const int8_t* __restrict__ f_wall, const R* __restrict__ fface, const R* __restrict__ fn,
+    const double* __restrict__ vol, double dt, const R* __restrict__ QA, R gm1, R* __restrict__ Rv,
+    R* __restrict__ D, R* __restrict__ hrs, R* __restrict__ dQ0) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  R qi[5];
+  state_of(QA, i, qi);
+  R dsum = R(0);
+  const int k0 = cf_ptr[i], k1 = cf_ptr[i + 1];
+  for (int k = k0; k < k1; ++k) {
+    R n[3], S, qp[5];
+    int wall;
+    const int64_t p = other_side(cf_idx[k], f_owner, f_nb, f_wall, fn, n, S, wall);
+    if (p >= 0) {
+      state_of(QA, p, qp);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) qp[v] = qi[v];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a == wall) qp[1 + a] = -qp[1 + a];
+    }
+    const R r = fmax(wave_speed(qi, n, gm1), wave_speed(qp, n, gm1));
+    hrs[k] = R(0.5) * r * S;
+    dsum += hrs[k];
+  }
+  R res[5];
+  if constexpr (std::is_same<R, float>::value) {
+    ff s[10];
+    face_sums_ff(k0, k1, cf_idx, fface, 0, s);
+    const ff h = ff_from(0.5 * dt);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const ff x = ff_add(s[v], ff_mul(h, s[5 + v]));
+      res[v] = x.h + x.l;
+    }
+  } else {
+    double s[10];
+    face_sums<double>(k0, k1, cf_idx, fface, s);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) res[v] = s[v] + 0.5 * dt * s[5 + v];
+  }
+  const R d = (R)(vol[i] / dt) + dsum;
+  D[i] = d;
+  const R id = R(1) / d;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    Rv[v * nc + i] = res[v];
+    dQ0[v * nc + i] = res[v] * id;
+  }
+}
+
+template <class R, bool kLast>
+__global__ void __launch_bounds__(256) k_jacobi_sweep(
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
+    const int8_t* __restrict__ f_wall, const R* __restrict__ fn, const R* __restrict__ QA,
+    const R* __restrict__ Rv, const R* __restrict__ D, const R* __restrict__ hrs,
+    const R* __restrict__ dQin, R* __restrict__ dQout, R* __restrict__ QAout, R gm1, int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
+  const int k0 = cf_ptr[i], k1 = cf_ptr[i + 1];
+  for (int k = k0; k < k1; ++k) {
+    R n[3], S, qp[5], dp[5], dT[5];
+    int wall;
+    const int64_t p = other_side(cf_idx[k], f_owner, f_nb, f_wall, fn, n, S, wall);
+    const int64_t c = p >= 0 ? p : i;
+    state_of(QA, c, qp);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dp[v] = dQin[v * nc + c];
+    if (p < 0) {  // mirror image of the cell
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (a == wall) {
+          qp[1 + a] = -qp[1 + a];
+          dp[1 + a] = -dp[1 + a];
+        }
+    }
+    euler_flux_change(qp, dp, n, gm1, dT);
+    const R h = hrs[k];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += R(0.5) * S * dT[v] - h * dp[v];
+  }
+  const R id = R(1) / D[i];
+  R d[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) d[v] = (Rv[v * nc + i] - acc[v]) * id;
+  if (!kLast) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dQout[v * nc + i] = d[v];
+    return;
+  }
+  // Q^{n+1} = Q^n + dQ, written to the other gather copy (neighbours still read Q^n)
+  if constexpr (std::is_same<R, float>::value) {
+    Gq<float> g;
+    g.load(QA, i);
+    ff q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = ff_add(ff{g.hi[v], g.lo[v]}, ff{d[v], 0.f});
+    Gq<float>::store_ff(QAout, i, q);
+    const float m2 = q[1].h * q[1].h + q[2].h * q[2].h + q[3].h * q[3].h;
+    if (!(q[0].h > 0.f && q[0].h * q[4].h > 0.5f * m2)) atomicOr(flag, kErrNonphysical);
+  } else {
+    Gq<double> g;
+    g.load(QA, i);
+    double q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = g.q[v] + d[v];
+    Gq<double>::store(QAout, i, q);
+    if (!physical(q)) atomicOr(flag, kErrNonphysical);
+  }
+}
+
 template <class R>
 __global__ void k_unpack(int64_t nc, const R* __restrict__ QA, double* __restrict__ Q) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -841,6 +1025,29 @@ void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage,
   }
 }
 template <class R>
+void launch_jacobi_init(const DevMesh& m, const R* fface, const R* fn, const double* vol,
+                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0, double gamma,
+                        cudaStream_t st) {
+  k_jacobi_init<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner,
+                                                          m.f_nb, m.f_wall, fface, fn, vol, dt,
+                                                          QA, (R)(gamma - 1.0), Rv, D, hrs, dQ0);
+}
+template <class R>
+void launch_jacobi_sweep(const DevMesh& m, const R* fn, const R* QA, const R* Rv, const R* D,
+                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout, double gamma,
+                         int* flag, cudaStream_t st) {
+  const unsigned nb = blocks_for(m.nc, 256);
+  const R gm1 = (R)(gamma - 1.0);
+  if (last)
+    k_jacobi_sweep<R, true><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner, m.f_nb,
+                                                m.f_wall, fn, QA, Rv, D, hrs, dQin, dQout, QAout,
+                                                gm1, flag);
+  else
+    k_jacobi_sweep<R, false><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner, m.f_nb,
+                                                 m.f_wall, fn, QA, Rv, D, hrs, dQin, dQout, QAout,
+                                                 gm1, flag);
+}
+template <class R>
 void launch_unpack(int64_t nc, const R* QA, double* Q, cudaStream_t st) {
   k_unpack<R><<<blocks_for(nc, 256), 256, 0, st>>>(nc, QA, Q);
 }
@@ -887,6 +1094,19 @@ template void launch_stage<double>(const DevMesh&, const GeoR<double>&, const do
 template void launch_stage<float>(const DevMesh&, const GeoR<float>&, const float*, int, double,
                                   void*, void*, float*, float*, int*, cudaStream_t);
 template void launch_unpack<double>(int64_t, const double*, double*, cudaStream_t);
+template void launch_jacobi_init<double>(const DevMesh&, const double*, const double*,
+                                         const double*, double, const double*, double*, double*,
+                                         double*, double*, double, cudaStream_t);
+template void launch_jacobi_init<float>(const DevMesh&, const float*, const float*, const double*,
+                                        double, const float*, float*, float*, float*, float*,
+                                        double, cudaStream_t);
+template void launch_jacobi_sweep<double>(const DevMesh&, const double*, const double*,
+                                          const double*, const double*, const double*,
+                                          const double*, double*, int, double*, double, int*,
+                                          cudaStream_t);
+template void launch_jacobi_sweep<float>(const DevMesh&, const float*, const float*, const float*,
+                                         const float*, const float*, const float*, float*, int,
+                                         float*, double, int*, cudaStream_t);
 template void launch_unpack<float>(int64_t, const float*, double*, cudaStream_t);
 
 }  // namespace gks
