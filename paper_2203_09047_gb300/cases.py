@@ -4,6 +4,7 @@
     python -m paper_2203_09047_gb300.cases tgv         # Taylor-Green vortex, Re 1600, Pr 0.72
     python -m paper_2203_09047_gb300.cases adjoint     # gradient through 200 S2O4 steps vs FD
     python -m paper_2203_09047_gb300.cases explosion   # spherical explosion, reflecting box
+    python -m paper_2203_09047_gb300.cases sod         # Sod shock tube vs the exact solution
 
 Each prints one JSON line per result.
 """
@@ -159,6 +160,121 @@ def adjoint(n=32, steps=200, every=20, ndirs=20, mu=1e-3, cfl=0.5, eps=1e-6, lay
     return rec
 
 
+def exact_riemann(left, right, x, t, x0=0.5, gamma=1.4):
+    """Exact solution (rho, u, p) at positions x and time t of the 1D Riemann problem with
+    left/right primitive states (rho, u, p) separated at x0: star pressure from
+    f_L(p) + f_R(p) + u_R - u_L = 0 (shock branch (p - p_K) sqrt(A_K / (p + B_K)), rarefaction
+    branch 2 c_K / (gamma - 1) ((p / p_K)^((gamma - 1) / (2 gamma)) - 1)) by Newton's method,
+    then the self-similar solution sampled at (x - x0)/t."""
+    g = gamma
+    rL, uL, pL = left
+    rR, uR, pR = right
+    cL, cR = np.sqrt(g * pL / rL), np.sqrt(g * pR / rR)
+
+    def fk(p, r, pk, ck):
+        if p > pk:
+            A, B = 2.0 / ((g + 1) * r), (g - 1) / (g + 1) * pk
+            sq = np.sqrt(A / (p + B))
+            return (p - pk) * sq, sq * (1.0 - 0.5 * (p - pk) / (B + p))
+        e = (g - 1) / (2 * g)
+        return 2 * ck / (g - 1) * ((p / pk) ** e - 1.0), (p / pk) ** (-(g + 1) / (2 * g)) / (r * ck)
+
+    p = max(1e-8, 0.5 * (pL + pR))
+    for _ in range(100):
+        fL, dL = fk(p, rL, pL, cL)
+        fR, dR = fk(p, rR, pR, cR)
+        dp = (fL + fR + uR - uL) / (dL + dR)
+        p = max(1e-10, p - dp)
+        if abs(dp) < 1e-15 * p:
+            break
+    fL, _ = fk(p, rL, pL, cL)
+    fR, _ = fk(p, rR, pR, cR)
+    us = 0.5 * (uL + uR) + 0.5 * (fR - fL)
+    g6 = (g - 1) / (g + 1)
+    xi = (np.asarray(x) - x0) / t
+    rho, u, pr = np.empty_like(xi), np.empty_like(xi), np.empty_like(xi)
+    for j, s in enumerate(xi):
+        if s <= us:  # left of the contact
+            if p > pL:
+                S = uL - cL * np.sqrt((g + 1) / (2 * g) * p / pL + (g - 1) / (2 * g))
+                st = (rL, uL, pL) if s < S else (rL * (p / pL + g6) / (g6 * p / pL + 1), us, p)
+            else:
+                cs = cL * (p / pL) ** ((g - 1) / (2 * g))
+                if s < uL - cL:
+                    st = (rL, uL, pL)
+                elif s > us - cs:
+                    st = (rL * (p / pL) ** (1 / g), us, p)
+                else:
+                    c = 2 / (g + 1) * (cL + 0.5 * (g - 1) * (uL - s))
+                    st = (rL * (c / cL) ** (2 / (g - 1)), 2 / (g + 1) * (cL + 0.5 * (g - 1) * uL + s),
+                          pL * (c / cL) ** (2 * g / (g - 1)))
+        else:
+            if p > pR:
+                S = uR + cR * np.sqrt((g + 1) / (2 * g) * p / pR + (g - 1) / (2 * g))
+                st = (rR, uR, pR) if s > S else (rR * (p / pR + g6) / (g6 * p / pR + 1), us, p)
+            else:
+                cs = cR * (p / pR) ** ((g - 1) / (2 * g))
+                if s > uR + cR:
+                    st = (rR, uR, pR)
+                elif s < us + cs:
+                    st = (rR * (p / pR) ** (1 / g), us, p)
+                else:
+                    c = 2 / (g + 1) * (cR - 0.5 * (g - 1) * (uR - s))
+                    st = (rR * (c / cR) ** (2 / (g - 1)), 2 / (g + 1) * (-cR + 0.5 * (g - 1) * uR + s),
+                          pR * (c / cR) ** (2 * g / (g - 1)))
+        rho[j], u[j], pr[j] = st
+    return rho, u, pr, p, us
+
+
+def sod(n=64, t_end=0.2, cfl=0.5, layers="hex", flux_mode=1, tau_model=1, jitter=0.0,
+        **weno):
+    """Sod's shock tube (Section 5, Riemann problems) along x in [0,1]^3 (reflecting walls at
+    x = 0, 1, which the waves do not reach by t = 0.2; periodic in y, z): left (1, 0, 1), right
+    (0.125, 0, 0.1) split at x = 0.5 by the cell's vertex mean; full flux, inviscid collision
+    time. Default: uniform hexahedra as the paper's hexahedral run. Density L1 error per unit
+    volume against the exact solution's cell averages (27-point quadrature), FP64 and mixed."""
+    import torch
+    m = I.layered_box_mesh(n, layers, lo=(0, 0, 0), hi=(1, 1, 1), bc=(1, 0, 0), jitter=jitter)
+    mesh = Mesh(m)
+    x = I.vertex_mean(m)
+    left = x[:, 0] < 0.5
+    rho0 = np.where(left, 1.0, 0.125)
+    p0 = np.where(left, 1.0, 0.1)
+    Q0 = np.ascontiguousarray(I.primitive_to_conserved(rho0, np.zeros((len(rho0), 3)), p0))
+    out = []
+    for prec, name in ((GKS_PREC_FP64, "fp64"), (GKS_PREC_MIXED, "mixed")):
+        rec = {"case": "sod", "mesh": layers, "precision": name, "cubes": n, "cells": mesh.n_cells,
+               "flux_mode": flux_mode, "tau_model": tau_model, "cfl": cfl, "jitter": jitter,
+               **weno}
+        try:
+            S = Solver(mesh, precision=prec, flux_mode=flux_mode, tau_model=tau_model, **weno)
+            S.set_state(Q0)
+            dt = S.max_dt(cfl)
+            nsteps = int(np.ceil(t_end / dt - 1e-12))
+            dt = t_end / nsteps
+            t0 = time.perf_counter()
+            S.step(dt, nsteps)
+            torch.cuda.synchronize()
+            rec["wall_s"] = time.perf_counter() - t0
+            Q = S.get_state().cpu().numpy()
+            xq, wq = S.cell_quadrature()
+            vol = wq.sum(axis=1)
+            re, _, _, ps, us = exact_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1),
+                                             xq[..., 0].ravel(), t_end)
+            ex = (re.reshape(wq.shape) * wq).sum(axis=1) / vol
+            rec.update({"steps": nsteps, "dt": dt, "p_star": ps, "u_star": us,
+                        "L1_rho": float((vol * np.abs(Q[0] - ex)).sum() / vol.sum()),
+                        "mass_drift": float(abs((vol * Q[0]).sum() - (vol * Q0[0]).sum()) /
+                                            (vol * Q0[0]).sum()),
+                        "status": "ok"})
+            S.close()
+        except GksError as e:
+            rec["status"] = f"stopped: {e}"
+        _emit(rec)
+        out.append(rec)
+    return out
+
+
 def explosion(n=32, t_end=0.25, cfl=0.5):
     """Spherical explosion in the reflecting box [-1,1]^3 (full flux, inviscid collision time):
     mass and energy drift per step and the mixed-vs-FP64 density difference."""
@@ -182,5 +298,12 @@ if __name__ == "__main__":
     kwargs = {}
     for a in sys.argv[2:]:
         k, v = a.split("=")
-        kwargs[k] = int(v) if v.isdigit() else v
-    {"advection": advection, "tgv": tgv, "adjoint": adjoint, "explosion": explosion}[which](**kwargs)
+        try:
+            kwargs[k] = int(v)
+        except ValueError:
+            try:
+                kwargs[k] = float(v)
+            except ValueError:
+                kwargs[k] = v
+    {"advection": advection, "tgv": tgv, "adjoint": adjoint, "explosion": explosion,
+     "sod": sod}[which](**kwargs)

@@ -432,8 +432,12 @@ __device__ __forceinline__ void load_coefs(const PolyRef<double>& c, int v, doub
 #ifndef GKS_FLUX_SMOOTH_MIN_BLOCKS
 #define GKS_FLUX_SMOOTH_MIN_BLOCKS 7  // resident 128-thread blocks per SM, FP32 smooth flux
 #endif
+#ifndef GKS_FLUX_FP64_MIN_BLOCKS
+#define GKS_FLUX_FP64_MIN_BLOCKS 1  // resident 128-thread blocks per SM, FP64 flux
+#endif
 template <class R, bool kFull, bool kTau0>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS) : 1)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS)
+                                                      : GKS_FLUX_FP64_MIN_BLOCKS)
     k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fgp, const R* __restrict__ poly,
