@@ -196,9 +196,8 @@ def run_implicit(gks, I, stream, torch, kmax=3, steps=10, warmup=3):
     for name, n, (lo, hi), bc, params, (p_cells, p_ms) in IMPLICIT_CASES:
         m = I.layered_box_mesh(n, "hybrid8", lo=lo, hi=hi, bc=bc)
         mesh = gks.Mesh(m)
-        if bc[0] == 1:  # gas at rest with a smooth perturbation in the walled box
-            rest = np.tile(np.array([1.0, 0.0, 0.0, 0.0, 2.5])[:, None], (1, mesh.n_cells))
-            Q0 = I.perturbed_state(rest, seed=7, amp=0.02)
+        if bc[0] == 1:  # gas at rest with a smooth bump in the walled box
+            Q0 = I.rest_bump_state(m)
         else:
             Q0 = I.advection_state(m)
         rec = {"cells": mesh.n_cells, "faces": mesh.n_faces, "kmax": kmax,

@@ -277,6 +277,14 @@ def explosion_state(mesh, gamma=1.4) -> np.ndarray:
     return np.ascontiguousarray(primitive_to_conserved(rho, np.zeros_like(x), p, gamma))
 
 
+def rest_bump_state(mesh, amp=0.02, width2=0.02, centre=(0.5, 0.5, 0.5), gamma=1.4) -> np.ndarray:
+    """Gas at rest (rho = 1, p = 1) with a smooth bump amp exp(-|x - centre|^2 / width2) added
+    to density and pressure, sampled at vertex means."""
+    x = vertex_mean(mesh)
+    b = amp * np.exp(-((x - np.asarray(centre)) ** 2).sum(axis=1) / width2)
+    return np.ascontiguousarray(primitive_to_conserved(1.0 + b, np.zeros_like(x), 1.0 + b, gamma))
+
+
 def perturbed_state(q: np.ndarray, seed: int, amp: float = 0.01) -> np.ndarray:
     """q + U(-amp, amp) on every entry, u from splitmix64 over (seed, flat index)."""
     u = uniform01(seed, np.arange(q.size, dtype=np.uint64)).reshape(q.shape)
