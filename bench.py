@@ -190,7 +190,7 @@ IMPLICIT_CASES = [
 ]
 
 
-def run_implicit(gks, I, stream, torch, kmax=3, steps=10, warmup=3):
+def run_implicit(gks, I, stream, torch, kmax=3, steps=20, warmup=3):
     """ms per implicit step (one residual + kmax Jacobi sweeps) for FP64 and mixed precision."""
     out = {}
     for name, n, (lo, hi), bc, params, (p_cells, p_ms) in IMPLICIT_CASES:
