@@ -150,18 +150,28 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 //   beta_0, tau, omega, omega-bar (Section 2), one variable per warp               (phase 3)
 //   C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m, i.e. Eq. weno as one polynomial (phase 4)
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
-// With kPf the tile's pseudo-inverse rows and sub-stencil entries (contiguous blocks of the
-// interleaved layouts) are brought into shared memory by two bulk copies issued when the block
+// With kPf the tile's pseudo-inverse rows and (FP32) sub-stencil entries, contiguous blocks of
+// the interleaved layouts, are brought into shared memory by bulk copies issued when the block
 // starts, so that their transfer overlaps phase 1; otherwise phase 2 reads them from global
 // memory.
 constexpr int kReconWarps = 5;
 constexpr int kReconThreads = kReconWarps * kTile;
 
+// Whether the sub-stencil entries travel with the rows in the bulk copies: yes for FP32; for
+// FP64 (twice the shared memory per tile) reading them from global memory measured 8 % faster
+// (5.26 against 5.73 ms per pass on the 64^3-cube mesh, more blocks per SM), for FP32 1 %
+// slower.
+template <class R>
+__host__ __device__ constexpr bool bulk_b() {
+  return sizeof(R) == 4;
+}
+
 // Shared-memory layout of one block for a range with largest stencil Kr, largest sum of
 // sub-stencil member counts Sr and largest number of sub-stencil slots Mr, in units of one
 // interleaved row (kTile values): [mbarrier, 16 B][A+ rows 9 Kr][B entries 4 Sr] (only with
-// kPf), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part starts on a 16-byte
-// boundary.
+// kPf; B only when bulk_b), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part
+// starts on a 16-byte boundary.
+
 template <class R>
 struct ReconSmem {
   size_t a_off, b_off, ca_off, cb_off, cbet_off, dq_off, bytes;
@@ -169,7 +179,7 @@ struct ReconSmem {
     const size_t row = (size_t)kTile * sizeof(R);
     a_off = pf ? 16 : 0;
     b_off = a_off + (pf ? 9 * (size_t)Kr * row : 0);
-    ca_off = b_off + (pf ? 4 * (size_t)Sr * row : 0);
+    ca_off = b_off + (pf && bulk_b<R>() ? 4 * (size_t)Sr * row : 0);
     cb_off = ca_off + 45 * row;
     cbet_off = cb_off + 15 * (size_t)Mr * row;
     dq_off = cbet_off + 5 * (size_t)Mr * row;
@@ -210,7 +220,8 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
   if (kPf) {
     if (threadIdx.x == 0) {
       mbar_init(bar);
-      const uint32_t ab = 9u * K * kTile * sizeof(R), bb = 4u * S * kTile * sizeof(R);
+      const uint32_t ab = 9u * K * kTile * sizeof(R),
+                     bb = bulk_b<R>() ? 4u * S * kTile * sizeof(R) : 0u;
       mbar_expect_tx(bar, ab + bb);
       bulk_load(smem_raw + L.a_off, Ag, ab, bar);
       if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
       return;
     }
     A = reinterpret_cast<const R*>(smem_raw + L.a_off) + lane;
-    Bt = reinterpret_cast<const R*>(smem_raw + L.b_off) + lane;
+    Bt = bulk_b<R>() ? reinterpret_cast<const R*>(smem_raw + L.b_off) + lane : Bg + lane;
   } else {
     __syncthreads();
     A = Ag + lane;
@@ -301,7 +312,8 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
     for (int j = 0; j < cs; ++j, e += 4 * kTile) {
       R c[4];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) c[t] = kPf ? e[t * kTile] : __ldg(e + t * kTile);
+      for (int t = 0; t < 4; ++t)
+        c[t] = kPf && bulk_b<R>() ? e[t * kTile] : __ldg(e + t * kTile);
       const int k = (int)c[3];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
