@@ -132,17 +132,21 @@ GKS_HD void slope_solve(R U, R V, R W, R lam, R K, const R b[5], R a[5]) {
 template <class R>
 struct Prim {
   R rho, U, V, W, p, lam;
+  R ir, ip, hil;  // 1/rho, 1/p, 1/(2 lam) = p/rho
 };
 
+// Primitives and the reciprocals the flux reuses (two divisions per state).
 template <class R>
 GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
   w.rho = q[0];
-  const R ir = R(1) / q[0];
-  w.U = q[1] * ir;
-  w.V = q[2] * ir;
-  w.W = q[3] * ir;
+  w.ir = R(1) / q[0];
+  w.U = q[1] * w.ir;
+  w.V = q[2] * w.ir;
+  w.W = q[3] * w.ir;
   w.p = (gamma - R(1)) * (q[4] - R(0.5) * (q[1] * w.U + q[2] * w.V + q[3] * w.W));
-  w.lam = R(0.5) * w.rho / w.p;
+  w.ip = R(1) / w.p;
+  w.lam = R(0.5) * w.rho * w.ip;
+  w.hil = w.p * w.ir;
   return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
 }
 
@@ -226,9 +230,8 @@ GKS_HD void half_init(const Prim<R>& w, R K, int s, Half<R>& h) {
   h.A = R(0.5) * k_erfc(-R(s) * sl * w.U);
   h.B = R(0.28209479177387814) * k_exp(-w.lam * w.U * w.U) / sl;  // 1/(2 sqrt(pi))
   h.A1 = w.U * h.A + R(s) * h.B;
-  const R hil = R(0.5) / w.lam;
-  h.A2 = w.U * h.A1 + hil * h.A;
-  h.S = w.V * w.V + w.W * w.W + (K + R(2)) * hil;
+  h.A2 = w.U * h.A1 + w.hil * h.A;
+  h.S = w.V * w.V + w.W * w.W + (K + R(2)) * w.hil;
 }
 template <class R>
 GKS_HD void half_moments(const Prim<R>& w, const Half<R>& h, R Q[5]) {
@@ -240,23 +243,25 @@ GKS_HD void half_moments(const Prim<R>& w, const Half<R>& h, R Q[5]) {
 }
 // Derivative of rho <psi> (half line) along the conserved increment dq, through the primitive
 // increments dU = (dm - U drho)/rho, dp = (gamma - 1)(dE - U . dm + |U|^2 drho / 2),
-// dlam = lam (drho/rho - dp/p), with dA = s B (2 lam dU + U dlam),
+// dlam/lam = drho/rho - dp/p, with dA = s B (2 lam dU + U dlam),
 // dB = -B (2 lam U dU + (U^2 + 1/(2 lam)) dlam). Equals rho <a psi> (half line) for the slope a
-// of the Maxwellian with rho <a psi> = dq over the full line.
+// of the Maxwellian with rho <a psi> = dq over the full line. No division: the reciprocals come
+// with the primitives.
 template <class R>
-GKS_HD void half_jvp(const Prim<R>& w, R ir, R gm1, R K, int s, const Half<R>& h, const R dq[5],
+GKS_HD void half_jvp(const Prim<R>& w, R gm1, R K, int s, const Half<R>& h, const R dq[5],
                      R dQ[5]) {
+  const R ir = w.ir, hil = w.hil;
   const R dU = (dq[1] - w.U * dq[0]) * ir, dV = (dq[2] - w.V * dq[0]) * ir,
           dW = (dq[3] - w.W * dq[0]) * ir;
   const R u2 = w.U * w.U + w.V * w.V + w.W * w.W;
   const R dp = gm1 * (dq[4] - (w.U * dq[1] + w.V * dq[2] + w.W * dq[3]) + R(0.5) * u2 * dq[0]);
-  const R dlam = w.lam * (dq[0] * ir - dp / w.p);
-  const R hil = R(0.5) / w.lam;
+  const R dll = dq[0] * ir - dp * w.ip;  // dlam / lam
+  const R dlam = w.lam * dll;
   const R dA = R(s) * h.B * (R(2) * w.lam * dU + w.U * dlam);
   const R dB = -h.B * (R(2) * w.lam * w.U * dU + (w.U * w.U + hil) * dlam);
   const R dA1 = dU * h.A + w.U * dA + R(s) * dB;
-  const R dA2 = dU * h.A1 + w.U * dA1 + hil * (dA - h.A * dlam / w.lam);
-  const R dS = R(2) * (w.V * dV + w.W * dW) - (K + R(2)) * hil * dlam / w.lam;
+  const R dA2 = dU * h.A1 + w.U * dA1 + hil * (dA - h.A * dll);
+  const R dS = R(2) * (w.V * dV + w.W * dW) - (K + R(2)) * hil * dll;
   dQ[0] = dq[0] * h.A + w.rho * dA;
   dQ[1] = dq[0] * h.A1 + w.rho * dA1;
   dQ[2] = dq[0] * w.V * h.A + w.rho * (dV * h.A + w.V * dA);
@@ -322,18 +327,18 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   if (!to_prim(q0, P.gamma, w0)) return false;
   // conserved-variable slopes of the interface equilibrium, dW_d = rho0 <ab_d psi>_0: the
   // half-space parts rho <a_d psi>_{u>0} + rho <a_d psi>_{u<0} of both sides' slopes
-  const R irl = R(1) / wl.rho, irr = R(1) / wr.rho;
+  const R irl = wl.ir, irr = wr.ir;
   R dW[3][5];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    half_jvp(wl, irl, gm1, P.K, +1, hl, dql[d], dW[d]);
-    half_jvp(wr, irr, gm1, P.K, -1, hr, dqr[d], t);
+    half_jvp(wl, gm1, P.K, +1, hl, dql[d], dW[d]);
+    half_jvp(wr, gm1, P.K, -1, hr, dqr[d], t);
 #pragma unroll
     for (int q = 0; q < 5; ++q) dW[d][q] += t[q];
   }
   // equilibrium time slope, rho0 <Ab psi>_0 = -sum_d rho0 <c_d ab_d psi>_0 = -sum_d A_d dW_d,
   // and the equilibrium flux moments E0 = rho0 <u psi>_0, E2 = rho0 <u Ab psi>_0 = A_x dWt
-  const R ir0 = R(1) / w0.rho, Ep0 = q0[4] + w0.p;
+  const R ir0 = w0.ir, Ep0 = q0[4] + w0.p;
   R dWt[5], E0[5], E1[5], E2[5];
   euler_jvp(w0, ir0, gm1, Ep0, 0, dW[0], dWt);
   euler_jvp(w0, ir0, gm1, Ep0, 1, dW[1], t);
