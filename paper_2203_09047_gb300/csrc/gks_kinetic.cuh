@@ -150,6 +150,33 @@ GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
   return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
 }
 
+// slope_solve and the full-line moments from a Prim (its 1/(2 lam)) and c4 = 4/(K + 3): the
+// same arithmetic without divisions.
+template <class R>
+GKS_HD void slope_solve_w(const Prim<R>& w, R K, R c4, const R b[5], R a[5]) {
+  const R U = w.U, V = w.V, W = w.W, lam = w.lam;
+  const R q2 = U * U + V * V + W * W;
+  const R e2 = q2 + (K + R(3)) * w.hil;
+  const R r1 = b[1] - U * b[0], r2 = b[2] - V * b[0], r3 = b[3] - W * b[0];
+  const R r4 = R(2) * b[4] - e2 * b[0];
+  a[4] = c4 * lam * lam * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
+  const R tl = R(2) * lam;
+  a[1] = tl * r1 - U * a[4];
+  a[2] = tl * r2 - V * a[4];
+  a[3] = tl * r3 - W * a[4];
+  a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * e2;
+}
+template <class R>
+GKS_HD void full_moments(const Prim<R>& w, R K, Mom<R>& M) {
+  const R hil = w.hil;
+  line_moments<R, 6>(w.V, hil, M.v);
+  line_moments<R, 6>(w.W, hil, M.w);
+  line_moments<R, 7>(w.U, hil, M.u);
+  M.xi[0] = R(1);
+  M.xi[1] = K * hil;
+  M.xi[2] = K * (K + R(2)) * hil * hil;
+}
+
 // Moments of an equilibrium in closed form. For a Maxwellian g(W) of the conserved state W,
 // dg = g (a . psi) with rho <a psi> = dW, so rho <c_d (a psi) psi> is the derivative of the
 // Euler flux along axis d applied to dW. euler_flux_x: rho <u psi> = F_x(W).
@@ -271,7 +298,7 @@ GKS_HD void half_jvp(const Prim<R>& w, R gm1, R K, int s, const Half<R>& h, cons
 // Moments of the half-line Maxwellian from its closed-form start (orders 0, 1).
 template <class R>
 GKS_HD void half_to_mom(const Prim<R>& w, R K, const Half<R>& h, Mom<R>& M) {
-  const R hil = R(0.5) / w.lam;
+  const R hil = w.hil;
   line_moments<R, 6>(w.V, hil, M.v);
   line_moments<R, 6>(w.W, hil, M.w);
   M.u[0] = h.A;
@@ -393,33 +420,34 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   // full flux: non-equilibrium parts need both sides' slopes, their time slopes and the
   // half-space moments
   R al[3][5], ar[3][5];
+  const R c4 = R(4) / (P.K + R(3));
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     R b[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) b[q] = dql[d][q] * irl;
-    slope_solve(wl.U, wl.V, wl.W, wl.lam, P.K, b, al[d]);
+    slope_solve_w(wl, P.K, c4, b, al[d]);
 #pragma unroll
     for (int q = 0; q < 5; ++q) b[q] = dqr[d][q] * irr;
-    slope_solve(wr.U, wr.V, wr.W, wr.lam, P.K, b, ar[d]);
+    slope_solve_w(wr, P.K, c4, b, ar[d]);
   }
   Mom<R> Mlp, Mrn;
   half_to_mom(wl, P.K, hl, Mlp);
   half_to_mom(wr, P.K, hr, Mrn);
   Mom<R> Ml, Mr;
-  maxwell_moments(wl.U, wl.V, wl.W, wl.lam, P.K, 0, Ml);
-  maxwell_moments(wr.U, wr.V, wr.W, wr.lam, P.K, 0, Mr);
+  full_moments(wl, P.K, Ml);
+  full_moments(wr, P.K, Mr);
   R Al[5], Ar[5];
   {
     R b[5];
     Gadotu(Ml, al, 0, b);
 #pragma unroll
     for (int q = 0; q < 5; ++q) b[q] = -b[q];
-    slope_solve(wl.U, wl.V, wl.W, wl.lam, P.K, b, Al);
+    slope_solve_w(wl, P.K, c4, b, Al);
     Gadotu(Mr, ar, 0, b);
 #pragma unroll
     for (int q = 0; q < 5; ++q) b[q] = -b[q];
-    slope_solve(wr.U, wr.V, wr.W, wr.lam, P.K, b, Ar);
+    slope_solve_w(wr, P.K, c4, b, Ar);
   }
   R cn[6], ct[6];
   if (tau > R(0)) {
