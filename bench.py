@@ -340,7 +340,7 @@ def run_gpu(args):
     # DRAM bytes (read + write) per pass from the ncu captures of the FP32 kernels on the
     # 48^3-cube mesh (profiles/k_recon_float_advection48_ncu.md,
     # profiles/k_flux_float_smooth_advection48_ncu.md), scaled by cells or faces
-    dram_per_unit = {"recon": (1435.8, nc), "flux": (321.3, nf)}
+    dram_per_unit = {"recon": (1435.8, nc), "flux": (322.4, nf)}
 
     def roof_for(table, is_mixed):
         dom = max(table, key=lambda k: table[k]["share"] or 0)
