@@ -150,33 +150,6 @@ GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
   return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
 }
 
-// slope_solve and the full-line moments from a Prim (its 1/(2 lam)) and c4 = 4/(K + 3): the
-// same arithmetic without divisions.
-template <class R>
-GKS_HD void slope_solve_w(const Prim<R>& w, R K, R c4, const R b[5], R a[5]) {
-  const R U = w.U, V = w.V, W = w.W, lam = w.lam;
-  const R q2 = U * U + V * V + W * W;
-  const R e2 = q2 + (K + R(3)) * w.hil;
-  const R r1 = b[1] - U * b[0], r2 = b[2] - V * b[0], r3 = b[3] - W * b[0];
-  const R r4 = R(2) * b[4] - e2 * b[0];
-  a[4] = c4 * lam * lam * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
-  const R tl = R(2) * lam;
-  a[1] = tl * r1 - U * a[4];
-  a[2] = tl * r2 - V * a[4];
-  a[3] = tl * r3 - W * a[4];
-  a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * e2;
-}
-template <class R>
-GKS_HD void full_moments(const Prim<R>& w, R K, Mom<R>& M) {
-  const R hil = w.hil;
-  line_moments<R, 6>(w.V, hil, M.v);
-  line_moments<R, 6>(w.W, hil, M.w);
-  line_moments<R, 7>(w.U, hil, M.u);
-  M.xi[0] = R(1);
-  M.xi[1] = K * hil;
-  M.xi[2] = K * (K + R(2)) * hil * hil;
-}
-
 // Moments of an equilibrium in closed form. For a Maxwellian g(W) of the conserved state W,
 // dg = g (a . psi) with rho <a psi> = dW, so rho <c_d (a psi) psi> is the derivative of the
 // Euler flux along axis d applied to dW. euler_flux_x: rho <u psi> = F_x(W).
@@ -295,19 +268,133 @@ GKS_HD void half_jvp(const Prim<R>& w, R gm1, R K, int s, const Half<R>& h, cons
   dQ[3] = dq[0] * w.W * h.A + w.rho * (dW * h.A + w.W * dA);
   dQ[4] = R(0.5) * (dq[0] * (h.A2 + h.S * h.A) + w.rho * (dA2 + dS * h.A + h.S * dA));
 }
-// Moments of the half-line Maxwellian from its closed-form start (orders 0, 1).
+
+// Half-line flux terms of the full flux in closed form. With the half-line moments
+// A_n = <u^n> (n = 0..4, A_{n+2} = U A_{n+1} + (n + 1) A_n / (2 lam)), the full-line moments of
+// v, w and xi^2 = K / (2 lam):
+//   F+(W)    = rho <u psi>     = rho (A1, A2, V A1, W A1, (A3 + S A1) / 2),
+//   T+_0(W)  = rho <u u psi>   = rho (A2, A3, V A2, W A2, (A4 + S A2) / 2),
+//   T+_1(W)  = rho <u v psi>   = rho (V A1, V A2, <v^2> A1, V W A1, (V A3 + Y_v A1) / 2),
+//   T+_2(W)  = rho <u w psi>   = rho (W A1, W A2, V W A1, <w^2> A1, (W A3 + Y_w A1) / 2),
+// S = V^2 + W^2 + (K + 2)/(2 lam), Y_v = V (V^2 + W^2 + (K + 4)/(2 lam)), Y_w likewise. Their
+// derivatives along a conserved increment dW are the half-line slope terms of Eq. flux-1:
+// rho <u (a psi) psi>_+ = DF+[dW] and rho <u c_d (a psi) psi>_+ = DT+_d[dW] for the slope a with
+// rho <a psi> = dW.
 template <class R>
-GKS_HD void half_to_mom(const Prim<R>& w, R K, const Half<R>& h, Mom<R>& M) {
-  const R hil = w.hil;
-  line_moments<R, 6>(w.V, hil, M.v);
-  line_moments<R, 6>(w.W, hil, M.w);
-  M.u[0] = h.A;
-  M.u[1] = h.A1;
+struct HalfLine {
+  R A[5], B;
+};
+template <class R>
+GKS_HD void half_line(const Prim<R>& w, const Half<R>& h, HalfLine<R>& m) {
+  m.A[0] = h.A;
+  m.A[1] = h.A1;
+  m.A[2] = h.A2;
+  m.A[3] = w.U * m.A[2] + R(2) * w.hil * m.A[1];
+  m.A[4] = w.U * m.A[3] + R(3) * w.hil * m.A[2];
+  m.B = h.B;
+}
+// Primitive increments along dq and the half-line moment increments dA[0..4].
+template <class R>
+struct DPrim {
+  R drho, dU, dV, dW, dlam, dhil;
+};
+template <class R>
+GKS_HD void dprim(const Prim<R>& w, R gm1, const R dq[5], DPrim<R>& d) {
+  const R ir = w.ir;
+  d.drho = dq[0];
+  d.dU = (dq[1] - w.U * dq[0]) * ir;
+  d.dV = (dq[2] - w.V * dq[0]) * ir;
+  d.dW = (dq[3] - w.W * dq[0]) * ir;
+  const R u2 = w.U * w.U + w.V * w.V + w.W * w.W;
+  const R dp = gm1 * (dq[4] - (w.U * dq[1] + w.V * dq[2] + w.W * dq[3]) + R(0.5) * u2 * dq[0]);
+  const R dll = dq[0] * ir - dp * w.ip;  // dlam / lam
+  d.dlam = w.lam * dll;
+  d.dhil = -w.hil * dll;
+}
+template <class R>
+GKS_HD void dhalf_line(const Prim<R>& w, int s, const HalfLine<R>& m, const DPrim<R>& d,
+                       R dA[5]) {
+  const R U = w.U, hil = w.hil;
+  dA[0] = R(s) * m.B * (R(2) * w.lam * d.dU + U * d.dlam);
+  const R dB = -m.B * (R(2) * w.lam * U * d.dU + (U * U + hil) * d.dlam);
+  dA[1] = d.dU * m.A[0] + U * dA[0] + R(s) * dB;
+  dA[2] = d.dU * m.A[1] + U * dA[1] + d.dhil * m.A[0] + hil * dA[0];
+  dA[3] = d.dU * m.A[2] + U * dA[2] + R(2) * (d.dhil * m.A[1] + hil * dA[1]);
+  dA[4] = d.dU * m.A[3] + U * dA[3] + R(3) * (d.dhil * m.A[2] + hil * dA[2]);
+}
+template <class R>
+GKS_HD void half_flux(const Prim<R>& w, R K, const HalfLine<R>& m, R F[5]) {
+  const R S = w.V * w.V + w.W * w.W + (K + R(2)) * w.hil;
+  F[0] = w.rho * m.A[1];
+  F[1] = w.rho * m.A[2];
+  F[2] = w.rho * w.V * m.A[1];
+  F[3] = w.rho * w.W * m.A[1];
+  F[4] = R(0.5) * w.rho * (m.A[3] + S * m.A[1]);
+}
+// DF+[dq]
+template <class R>
+GKS_HD void half_flux_jvp(const Prim<R>& w, R gm1, R K, int s, const HalfLine<R>& m,
+                          const R dq[5], R out[5]) {
+  DPrim<R> d;
+  dprim(w, gm1, dq, d);
+  R dA[5];
+  dhalf_line(w, s, m, d, dA);
+  const R S = w.V * w.V + w.W * w.W + (K + R(2)) * w.hil;
+  const R dS = R(2) * (w.V * d.dV + w.W * d.dW) + (K + R(2)) * d.dhil;
+  out[0] = d.drho * m.A[1] + w.rho * dA[1];
+  out[1] = d.drho * m.A[2] + w.rho * dA[2];
+  out[2] = d.drho * w.V * m.A[1] + w.rho * (d.dV * m.A[1] + w.V * dA[1]);
+  out[3] = d.drho * w.W * m.A[1] + w.rho * (d.dW * m.A[1] + w.W * dA[1]);
+  out[4] = R(0.5) * (d.drho * (m.A[3] + S * m.A[1]) +
+                     w.rho * (dA[3] + dS * m.A[1] + S * dA[1]));
+}
+// DT+_k[dq] for the velocity component k (0 normal, 1, 2 tangential)
+template <class R>
+GKS_HD void half_second_jvp(const Prim<R>& w, R gm1, R K, int s, const HalfLine<R>& m, int k,
+                            const R dq[5], R out[5]) {
+  DPrim<R> d;
+  dprim(w, gm1, dq, d);
+  R dA[5];
+  dhalf_line(w, s, m, d, dA);
+  const R V = w.V, W = w.W, hil = w.hil;
+  R t[5], dt[5];
+  if (k == 0) {
+    const R S = V * V + W * W + (K + R(2)) * hil;
+    const R dS = R(2) * (V * d.dV + W * d.dW) + (K + R(2)) * d.dhil;
+    t[0] = m.A[2];
+    dt[0] = dA[2];
+    t[1] = m.A[3];
+    dt[1] = dA[3];
+    t[2] = V * m.A[2];
+    dt[2] = d.dV * m.A[2] + V * dA[2];
+    t[3] = W * m.A[2];
+    dt[3] = d.dW * m.A[2] + W * dA[2];
+    t[4] = R(0.5) * (m.A[4] + S * m.A[2]);
+    dt[4] = R(0.5) * (dA[4] + dS * m.A[2] + S * dA[2]);
+  } else {
+    // c = the tangential component k, o = the other one
+    const R c = k == 1 ? V : W, o = k == 1 ? W : V;
+    const R dc = k == 1 ? d.dV : d.dW, dO = k == 1 ? d.dW : d.dV;
+    const R c2 = c * c + hil, dc2 = R(2) * c * dc + d.dhil;  // <c^2>
+    const R q = V * V + W * W + (K + R(4)) * hil;
+    const R dqq = R(2) * (V * d.dV + W * d.dW) + (K + R(4)) * d.dhil;
+    const R Y = c * q, dY = dc * q + c * dqq;
+    t[0] = c * m.A[1];
+    dt[0] = dc * m.A[1] + c * dA[1];
+    t[1] = c * m.A[2];
+    dt[1] = dc * m.A[2] + c * dA[2];
+    // momentum components along this tangential axis and the other one
+    const R tc = c2 * m.A[1], dtc = dc2 * m.A[1] + c2 * dA[1];
+    const R to = c * o * m.A[1], dto = (dc * o + c * dO) * m.A[1] + c * o * dA[1];
+    t[2] = k == 1 ? tc : to;
+    dt[2] = k == 1 ? dtc : dto;
+    t[3] = k == 1 ? to : tc;
+    dt[3] = k == 1 ? dto : dtc;
+    t[4] = R(0.5) * (c * m.A[3] + Y * m.A[1]);
+    dt[4] = R(0.5) * (dc * m.A[3] + c * dA[3] + dY * m.A[1] + Y * dA[1]);
+  }
 #pragma unroll
-  for (int n = 2; n < 7; ++n) M.u[n] = w.U * M.u[n - 1] + R(n - 1) * hil * M.u[n - 2];
-  M.xi[0] = R(1);
-  M.xi[1] = K * hil;
-  M.xi[2] = K * (K + R(2)) * hil * hil;
+  for (int q2 = 0; q2 < 5; ++q2) out[q2] = d.drho * t[q2] + w.rho * dt[q2];
 }
 
 template <class R>
@@ -417,37 +504,45 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
     }
     return true;
   }
-  // full flux: non-equilibrium parts need both sides' slopes, their time slopes and the
-  // half-space moments
-  R al[3][5], ar[3][5];
-  const R c4 = R(4) / (P.K + R(3));
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    R b[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = dql[d][q] * irl;
-    slope_solve_w(wl, P.K, c4, b, al[d]);
-#pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = dqr[d][q] * irr;
-    slope_solve_w(wr, P.K, c4, b, ar[d]);
-  }
-  Mom<R> Mlp, Mrn;
-  half_to_mom(wl, P.K, hl, Mlp);
-  half_to_mom(wr, P.K, hr, Mrn);
-  Mom<R> Ml, Mr;
-  full_moments(wl, P.K, Ml);
-  full_moments(wr, P.K, Mr);
-  R Al[5], Ar[5];
+  // full flux: the non-equilibrium parts of both sides. With the side's slopes a_d (rho <a_d psi>
+  // = dq_d) and time slope A (rho <A psi> = -sum_d A_d(W) dq_d, Euler Jacobians at the side's
+  // state): N0 = F+(W), N1 = sum_d DT+_d[dq_d] = rho <u (a . c) psi>_+, N2 = DF+[rho <A psi>]
+  // = rho <u A psi>_+ (half line u > 0 on the left, u < 0 on the right)
+  R NL[3][5], NR[3][5];
   {
-    R b[5];
-    Gadotu(Ml, al, 0, b);
+    HalfLine<R> ml, mr;
+    half_line(wl, hl, ml);
+    half_line(wr, hr, mr);
+    half_flux(wl, P.K, ml, NL[0]);
+    half_flux(wr, P.K, mr, NR[0]);
+    R dtl[5], dtr[5];
+    const R Epl = ql[4] + wl.p, Epr = qr[4] + wr.p;
+    euler_jvp(wl, irl, gm1, Epl, 0, dql[0], dtl);
+    euler_jvp(wr, irr, gm1, Epr, 0, dqr[0], dtr);
+    half_second_jvp(wl, gm1, P.K, +1, ml, 0, dql[0], NL[1]);
+    half_second_jvp(wr, gm1, P.K, -1, mr, 0, dqr[0], NR[1]);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = -b[q];
-    slope_solve_w(wl, P.K, c4, b, Al);
-    Gadotu(Mr, ar, 0, b);
+    for (int d = 1; d < 3; ++d) {
+      euler_jvp(wl, irl, gm1, Epl, d, dql[d], t);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) b[q] = -b[q];
-    slope_solve_w(wr, P.K, c4, b, Ar);
+      for (int q = 0; q < 5; ++q) dtl[q] += t[q];
+      euler_jvp(wr, irr, gm1, Epr, d, dqr[d], t);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) dtr[q] += t[q];
+      half_second_jvp(wl, gm1, P.K, +1, ml, d, dql[d], t);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) NL[1][q] += t[q];
+      half_second_jvp(wr, gm1, P.K, -1, mr, d, dqr[d], t);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) NR[1][q] += t[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      dtl[q] = -dtl[q];
+      dtr[q] = -dtr[q];
+    }
+    half_flux_jvp(wl, gm1, P.K, +1, ml, dtl, NL[2]);
+    half_flux_jvp(wr, gm1, P.K, -1, mr, dtr, NR[2]);
   }
   R cn[6], ct[6];
   if (tau > R(0)) {
@@ -466,23 +561,16 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
     cn[0] = R(1);
     ct[2] = R(1);
   }
-  R nl0[5], nl1[5], nl2[5], nr0[5], nr1[5], nr2[5];
-  G(Mlp, 1, 0, 0, 0, nl0);
-  Gadotu(Mlp, al, 1, nl1);
-  Ga(Mlp, Al, 1, 0, 0, nl2);
-  G(Mrn, 1, 0, 0, 0, nr0);
-  Gadotu(Mrn, ar, 1, nr1);
-  Ga(Mrn, Ar, 1, 0, 0, nr2);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const R geq_n = cn[0] * E0[q] + cn[1] * E1[q] + cn[2] * E2[q];
     const R geq_t = ct[0] * E0[q] + ct[1] * E1[q] + ct[2] * E2[q];
-    const R gl_n = cn[3] * nl0[q] + cn[4] * nl1[q] + cn[5] * nl2[q];
-    const R gl_t = ct[3] * nl0[q] + ct[4] * nl1[q] + ct[5] * nl2[q];
-    const R gr_n = cn[3] * nr0[q] + cn[4] * nr1[q] + cn[5] * nr2[q];
-    const R gr_t = ct[3] * nr0[q] + ct[4] * nr1[q] + ct[5] * nr2[q];
-    Fn[q] = geq_n + wl.rho * gl_n + wr.rho * gr_n;
-    Ft[q] = geq_t + wl.rho * gl_t + wr.rho * gr_t;
+    const R gl_n = cn[3] * NL[0][q] + cn[4] * NL[1][q] + cn[5] * NL[2][q];
+    const R gl_t = ct[3] * NL[0][q] + ct[4] * NL[1][q] + ct[5] * NL[2][q];
+    const R gr_n = cn[3] * NR[0][q] + cn[4] * NR[1][q] + cn[5] * NR[2][q];
+    const R gr_t = ct[3] * NR[0][q] + ct[4] * NR[1][q] + ct[5] * NR[2][q];
+    Fn[q] = geq_n + gl_n + gr_n;
+    Ft[q] = geq_t + gl_t + gr_t;
   }
   return true;
 }
