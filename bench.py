@@ -45,6 +45,7 @@ def parse():
                     help="timed steps of the FP64 path (default: steps // 4, at least 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-vjp", action="store_true", help="skip the residual VJP timing")
     ap.add_argument("--no-implicit", action="store_true",
                     help="skip the implicit (Jacobi) workloads reported beside the headline")
     return ap.parse_args()
@@ -181,6 +182,26 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def run_vjp(gks, I, S, Q0, dt, torch, stream, calls=3):
+    """ms per residual VJP (gks_residual_vjp: FP64 reconstruction recomputed, then the reverse
+    passes of the flux, polynomial evaluation, reconstruction and stencil gathers)."""
+    Q = torch.from_numpy(np.ascontiguousarray(Q0)).cuda()
+    d = I.normal_directions(Q0.shape, 2, 5)
+    gL, gLt = torch.from_numpy(d[0]).cuda(), torch.from_numpy(d[1]).cuda()
+    gQ = torch.empty_like(Q)
+    gks.gks_residual_vjp(S.h, Q, dt, gL, gLt, gQ)  # warm-up (allocates the adjoint buffers)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(calls):
+        gks.gks_residual_vjp(S.h, Q, dt, gL, gLt, gQ)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / calls
+    return {"ms_per_call": ms, "cells_per_s": S.n_cells / (ms * 1e-3), "calls": calls,
+            "dtype": "f64", "api": "gks_residual_vjp (device buffers)"}
+
+
 IMPLICIT_CASES = [
     # name, cubes, layers box, bc, params, paper (cells, ms per step) for context
     ("cavity_like", 32, ((0, 0, 0), (1, 1, 1)), (1, 1, 1),
@@ -397,6 +418,10 @@ def run_gpu(args):
         line["e2e"] = {"value": nc * 2 * e_steps / el, "unit": UNIT, "steps": e_steps,
                        "h2d_bytes_per_step": int(Qh.numel() * 8), "d2h_bytes_per_step": int(Qo.numel() * 8),
                        "api": "gks_set_state(host) + gks_step + gks_get_state(host)"}
+
+    # the residual's vector-Jacobian product on the same mesh and state (FP64)
+    if not args.no_vjp:
+        line["vjp"] = run_vjp(gks, I, fp64["solver"], Q0, mixed["dt"], torch, stream)
 
     # the implicit Jacobi path (Section 4) on workloads sized like the paper's two timed cases,
     # reported beside the headline with the paper's own times (TITAN RTX, FP64) as context
