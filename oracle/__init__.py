@@ -17,20 +17,30 @@ _LIB = os.path.join(_HERE, "liboracle_gks.so")
 _lib = None
 
 # Parameter vector layout: gamma, mu, Pr, flux_mode, tau_model, tau_eps, tau_C, weno_gamma,
-# weno_eps, weno_pow, weno_linear.
+# weno_eps, weno_pow, weno_linear, T_ref, mu_pow, then per wall plane (axis + 3 side, side 1 the
+# upper plane) the wall velocity (3) and temperature (<= 0: adiabatic).
 DEFAULTS = dict(gamma=1.4, mu=0.0, Pr=1.0, flux_mode=0, tau_model=0, tau_eps=0.01, tau_C=1.0,
-                weno_gamma=0.0125, weno_eps=1e-8, weno_pow=1, weno_linear=0)
+                weno_gamma=0.0125, weno_eps=1e-8, weno_pow=1, weno_linear=0, T_ref=1.0,
+                mu_pow=0.7)
 _ORDER = ["gamma", "mu", "Pr", "flux_mode", "tau_model", "tau_eps", "tau_C", "weno_gamma",
-          "weno_eps", "weno_pow", "weno_linear"]
+          "weno_eps", "weno_pow", "weno_linear", "T_ref", "mu_pow"]
 
 
-def params_vec(**kw) -> np.ndarray:
+def params_vec(wall_u=None, wall_T=None, **kw) -> np.ndarray:
+    """wall_u [6][3] and wall_T [6]: velocity and temperature of each wall plane (axis + 3 side);
+    zero velocity and adiabatic walls by default."""
     d = dict(DEFAULTS)
     for k, v in kw.items():
         if k not in d:
             raise KeyError(k)
         d[k] = v
-    return np.array([float(d[k]) for k in _ORDER], dtype=np.float64)
+    walls = np.zeros((6, 4))
+    if wall_u is not None:
+        walls[:, :3] = np.asarray(wall_u, dtype=np.float64).reshape(6, 3)
+    if wall_T is not None:
+        walls[:, 3] = np.asarray(wall_T, dtype=np.float64).reshape(6)
+    return np.concatenate([np.array([float(d[k]) for k in _ORDER], dtype=np.float64),
+                           walls.ravel()])
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +76,7 @@ def lib():
         L.oracle_reconstruct_at.argtypes = [P, D, D, ctypes.c_int, I, D, D]
         L.oracle_gp_flux.argtypes = [D, D, D, D, D, ctypes.c_double, D]
         L.oracle_time_coeffs.argtypes = [ctypes.c_double, ctypes.c_double, D]
+        L.oracle_wall_ghost.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D, D]
         L.oracle_slope.argtypes = [ctypes.c_double] * 5 + [D, D]
         L.oracle_residual.argtypes = [P, D, D, ctypes.c_double, D, D, ctypes.c_char_p, ctypes.c_int]
         L.oracle_residual_jvp.argtypes = [P, D, D, D, ctypes.c_double, D, D, D, D]
@@ -227,6 +238,16 @@ def gp_flux(params, ql, dql, qr, dqr, dt):
     if st:
         raise OracleError(st)
     return F
+
+
+def wall_ghost(params, kind, plane, v, g):
+    """Ghost value and gradient (global frame, g[5][3] = d v_r / d x_b) at a point of a wall of
+    the given kind (1 slip, 2 no-slip) on plane axis + 3 side."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(5, 3)
+    vg, gg = np.zeros(5), np.zeros((5, 3))
+    lib().oracle_wall_ghost(_d(params), int(kind), int(plane), _d(v), _d(g), _d(vg), _d(gg))
+    return vg, gg
 
 
 def time_coeffs(tau, delta):

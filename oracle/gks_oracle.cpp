@@ -27,8 +27,16 @@
 //  * time integrals F(dt/2), F(dt) of the face flux give F^n and dF/dt by the two-point fit;
 //  * two-stage fourth-order update: Q* = Q + dt/2 L + dt^2/8 Lt,
 //    Q^{n+1} = Q + dt L + dt^2/6 (Lt + 2 Lt*) (Section 3.3, the cited two-stage method);
-//  * reflecting walls: the ghost is the mirror image of the owner; the wall flux has its mass,
-//    energy and tangential-momentum components set to zero;
+//  * reflecting (slip) walls: the ghost is the mirror image of the owner; the wall flux has its
+//    mass, energy and tangential-momentum components set to zero;
+//  * no-slip walls (Section 5 names adiabatic and isothermal ones, without formulas): ghost cells
+//    in the stencils carry all three velocity components negated (the stationary adiabatic
+//    wall); at the wall's Gauss points the ghost is rho_g = rho, U_g = 2 U_w - U with p_g = p
+//    (adiabatic) or T_g = 2 T_w - p/rho (isothermal), its gradient the mirrored gradient mapped
+//    by the Jacobian of that map; the wall flux has no mass component and, at an adiabatic wall,
+//    the energy component U_w . (momentum flux);
+//  * power-law viscosity (Section 5.4): tau = mu (T0/T_ref)^mu_pow / p0 + C dp dt with
+//    T0 = p0 / rho0 of the interface equilibrium;
 //  * implicit step (Section 4): the system is written with |Omega_i| (the printed Eq. jacobi
 //    drops the volume of the residual's definition), Res is the GKS residual averaged over the
 //    step, r_f = max over both sides of |U . n| + c at Q^n, S_f n_f the face's area vector.
@@ -71,6 +79,11 @@ inline Dual erfc(Dual a) {
 inline Dual fabs(Dual a) { return a.v < 0 ? -a : a; }
 inline double val(double a) { return a; }
 inline double val(Dual a) { return a.v; }
+inline Dual pow(Dual a, double e) {
+  const double p = std::pow(a.v, e);
+  return {p, e * p / a.v * a.d};
+}
+using std::pow;
 using std::exp;
 using std::sqrt;
 using std::erfc;
@@ -78,9 +91,16 @@ using std::fabs;
 
 // ---------------------------------------------------------------------------------------------
 // Affine per-axis transforms x' = s x + t (periodic shifts and mirror images).
+// The flow variables of an image carry the boundary conditions of the wall planes it was
+// reflected across (Section 2: ghost geometry by mirror images, flow variables from the boundary
+// condition). `walls` lists those planes (axis + 3 side) in the order the reflections apply;
+// bit j of vflip records whether the j-th velocity component ends up negated. Images that
+// coincide geometrically are one member (the first path found is kept).
 struct Xform {
   double s[3] = {1, 1, 1};
   double t[3] = {0, 0, 0};
+  int vflip = 0;
+  int nw = 0, walls[8];  // at most two walls per member: a face and a face of a neighbour
 };
 Xform compose(const Xform& a, const Xform& b) {  // a after b
   Xform c;
@@ -88,6 +108,9 @@ Xform compose(const Xform& a, const Xform& b) {  // a after b
     c.s[k] = a.s[k] * b.s[k];
     c.t[k] = a.s[k] * b.t[k] + a.t[k];
   }
+  c.vflip = a.vflip ^ b.vflip;
+  for (int k = 0; k < b.nw && c.nw < 8; ++k) c.walls[c.nw++] = b.walls[k];
+  for (int k = 0; k < a.nw && c.nw < 8; ++k) c.walls[c.nw++] = a.walls[k];
   return c;
 }
 bool same_xform(const Xform& a, const Xform& b, double tol) {
@@ -295,11 +318,13 @@ void solve5(T A[5][5], T b[5], T x[5]) {
 struct Params {
   double gamma, mu, Pr;
   int flux_mode;  // 0 smooth (Eq. flux-2), 1 full (Eq. flux-1)
-  int tau_model;  // 0 zero, 1 inviscid, 2 viscous
+  int tau_model;  // 0 zero, 1 inviscid, 2 viscous, 3 viscous with power-law mu(T)
   double tau_eps, tau_C;
   double weno_gamma, weno_eps;
   int weno_pow;
   int weno_linear;  // 1: use the linear weights (omega-bar = gamma), i.e. plain P0
+  double T_ref, mu_pow;   // mu(T) = mu (T / T_ref)^mu_pow, T = p / rho (Section 5.4)
+  double uw[6][3], Tw[6];  // per wall plane (axis + 3 side): velocity, temperature (<= 0: adiabatic)
 };
 Params read_params(const double* p) {
   Params q;
@@ -314,6 +339,12 @@ Params read_params(const double* p) {
   q.weno_eps = p[8];
   q.weno_pow = (int)p[9];
   q.weno_linear = (int)p[10];
+  q.T_ref = p[11];
+  q.mu_pow = p[12];
+  for (int w = 0; w < 6; ++w) {
+    for (int a = 0; a < 3; ++a) q.uw[w][a] = p[13 + 4 * w + a];
+    q.Tw[w] = p[13 + 4 * w + 3];
+  }
   return q;
 }
 
@@ -327,6 +358,8 @@ struct Face {
   int owner = -1, owner_face = -1, nb = -1, nb_face = -1;
   Xform nb_to_owner;  // neighbour frame -> owner frame (for a wall: the mirror image)
   int wall_axis = -1;
+  int wall_kind = 0;   // 1 slip, 2 no-slip (the box condition of its axis)
+  int wall_plane = -1;  // axis + 3 side (side 1: the upper plane)
   double xg[4][3], n[4][3], w[4];  // Gauss points (owner frame), unit normals, area weights
   double area = 0.0;
 };
@@ -540,7 +573,7 @@ int build_mesh(Mesh& m, bool lazy) {
       int axis = -1;
       double plane = 0;
       for (int a = 0; a < 3 && axis < 0; ++a) {
-        if (m.bc[a] != 1) continue;
+        if (m.bc[a] != 1 && m.bc[a] != 2) continue;
         for (double pl : {m.lo[a], m.hi[a]}) {
           bool on = true;
           for (int v : vo)
@@ -558,8 +591,13 @@ int build_mesh(Mesh& m, bool lazy) {
       }
       f.nb = -1;
       f.wall_axis = axis;
+      f.wall_kind = m.bc[axis];
+      f.wall_plane = axis + (std::fabs(plane - m.hi[axis]) <= tol ? 3 : 0);
       f.nb_to_owner.s[axis] = -1.0;
       f.nb_to_owner.t[axis] = 2.0 * plane;
+      f.nb_to_owner.vflip = f.wall_kind == 1 ? 1 << axis : 7;
+      f.nb_to_owner.nw = 1;
+      f.nb_to_owner.walls[0] = f.wall_plane;
     }
     // orient the owner-side vertex list outward, rotate the smallest node id first
     auto coords = [&](const std::vector<int>& ids, double V[4][3]) {
@@ -702,11 +740,26 @@ struct Recon {
   int M;
 };
 
+// Flow variables of an image: the wall maps of its planes applied in order. Slip: the normal
+// momentum negated. No-slip with velocity U_w (the reconstruction takes every no-slip wall as
+// adiabatic): rho_g = rho, m_g = 2 U_w rho - m, E_g = E + 2 |U_w|^2 rho - 2 U_w . m (the same
+// density and pressure, U_g = 2 U_w - U). Periodic images keep the state.
 template <class T>
-void transform_state(const Xform& X, const T* q, T* out) {
-  out[0] = q[0];
-  for (int a = 0; a < 3; ++a) out[1 + a] = X.s[a] < 0 ? -q[1 + a] : q[1 + a];
-  out[4] = q[4];
+void transform_state(const Mesh& m, const Params& P, const Xform& X, const T* q, T* out) {
+  for (int v = 0; v < 5; ++v) out[v] = q[v];
+  for (int k = 0; k < X.nw; ++k) {
+    const int pl = X.walls[k], ax = pl % 3;
+    if (m.bc[ax] == 1) {
+      out[1 + ax] = -out[1 + ax];
+      continue;
+    }
+    const double* uw = P.uw[pl];
+    const double uw2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+    T um = T(0.0);
+    for (int a = 0; a < 3; ++a) um += uw[a] * out[1 + a];
+    out[4] = out[4] + 2.0 * uw2 * out[0] - 2.0 * um;
+    for (int a = 0; a < 3; ++a) out[1 + a] = 2.0 * uw[a] * out[0] - out[1 + a];
+  }
 }
 
 template <class T>
@@ -724,7 +777,7 @@ void reconstruct_cell(const Mesh& m, const Params& P, const T* Q, int n, int i, 
     const Member& mb = ci.stencil[k];
     T qk[5], qt[5];
     for (int v = 0; v < 5; ++v) qk[v] = Q[v * (size_t)n + mb.cell];
-    transform_state(mb.T, qk, qt);
+    transform_state(m, P, mb.T, qk, qt);
     for (int v = 0; v < 5; ++v) dq[k + (size_t)v * K] = qt[v] - r.Q0[v];
   }
   // cell quadrature for the smoothness indicators
@@ -950,6 +1003,14 @@ void time_coeffs(T tau, double d, T c[6]) {
   c[5] = -tau * tau * (1.0 - e);
 }
 
+// Dynamic viscosity at temperature T = p / rho: mu (T / T_ref)^mu_pow for the power law of
+// Section 5.4 (collision-time model 3), mu otherwise.
+template <class T>
+T viscosity(const Params& P, T temp) {
+  if (P.tau_model == 3) return P.mu * pow(temp / P.T_ref, P.mu_pow);
+  return T(P.mu);
+}
+
 // Local-frame flux at one Gauss point. dq*[m][v] = derivative of conserved variable v along n_m.
 // Outputs the time integrals F(dt/2) and F(dt). Returns false for a non-physical state.
 template <class T>
@@ -1015,6 +1076,7 @@ bool gp_flux(const Params& P, const T ql[5], const T dql[3][5], const T qr[5], c
   const T dp = fabs((wl.p - wr.p) / (wl.p + wr.p));
   if (P.tau_model == 1) tau = P.tau_eps * dt + P.tau_C * dp * dt;
   if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
+  if (P.tau_model == 3) tau = viscosity(P, w0.p / w0.rho) / w0.p + P.tau_C * dp * dt;
   // flux moments
   const Poly<T> u1 = mono<T>(1, 0, 0);
   T e0[5], e1[5], e2[5], nl0[5], nl1[5], nl2[5], nr0[5], nr1[5], nr2[5];
@@ -1135,6 +1197,62 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
   return ST_OK;
 }
 
+// Ghost state at a wall point (Section 2: the ghost's flow variables follow the boundary
+// condition; the paper names slip, no-slip adiabatic and no-slip isothermal walls in Section 5
+// and gives no formulas). From the owner's value v and gradient g at the point (global frame),
+// the image across the plane of axis a: geometry mirrored, so d/dx_a changes sign, and
+//   slip:               the normal momentum negated;
+//   no-slip (U_w, T_w): rho_g = rho, U_g = 2 U_w - U, and
+//     adiabatic (T_w <= 0): p_g = p, i.e. E_g = E + 2 rho |U_w|^2 - 2 U_w . m,
+//     isothermal:           T_g = 2 T_w - T with T = p / rho, i.e.
+//                           E_g = 2 rho T_w / (gamma-1) - E + |m|^2/rho + 2 rho |U_w|^2 - 2 U_w . m.
+// The ghost gradient is the mirrored gradient mapped by the Jacobian of that map at v.
+template <class T>
+void wall_ghost(const Params& P, int kind, int plane, const T* v, const T g[5][3], T* vg,
+                T gg[5][3]) {
+  const int ax = plane % 3;
+  T J[5][5];
+  for (int r = 0; r < 5; ++r)
+    for (int c = 0; c < 5; ++c) J[r][c] = T(r == c ? 1.0 : 0.0);
+  if (kind == 1) {
+    J[1 + ax][1 + ax] = T(-1.0);
+    for (int r = 0; r < 5; ++r) vg[r] = v[r];
+    vg[1 + ax] = -v[1 + ax];
+  } else {
+    const double* uw = P.uw[plane];
+    const double Tw = P.Tw[plane];
+    const double uw2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+    const T rho = v[0];
+    T um = T(0.0);
+    for (int a = 0; a < 3; ++a) um += uw[a] * v[1 + a];
+    vg[0] = rho;
+    for (int a = 0; a < 3; ++a) {
+      vg[1 + a] = 2.0 * uw[a] * rho - v[1 + a];
+      J[1 + a][0] = T(2.0 * uw[a]);
+      J[1 + a][1 + a] = T(-1.0);
+    }
+    if (Tw <= 0.0) {
+      vg[4] = v[4] + 2.0 * uw2 * rho - 2.0 * um;
+      J[4][0] = T(2.0 * uw2);
+      for (int a = 0; a < 3; ++a) J[4][1 + a] = T(-2.0 * uw[a]);
+    } else {
+      T m2 = T(0.0);
+      for (int a = 0; a < 3; ++a) m2 += v[1 + a] * v[1 + a];
+      const T U2 = m2 / (rho * rho);
+      vg[4] = 2.0 * Tw / (P.gamma - 1.0) * rho - v[4] + m2 / rho + 2.0 * uw2 * rho - 2.0 * um;
+      J[4][0] = 2.0 * Tw / (P.gamma - 1.0) - U2 + 2.0 * uw2;
+      for (int a = 0; a < 3; ++a) J[4][1 + a] = 2.0 * v[1 + a] / rho - 2.0 * uw[a];
+      J[4][4] = T(-1.0);
+    }
+  }
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) {
+      T x = T(0.0);
+      for (int c = 0; c < 5; ++c) x += J[r][c] * g[c][b];
+      gg[r][b] = b == ax ? -x : x;
+    }
+}
+
 // Face flux (Eq. flux-qud over the 2x2 Gauss points) fitted in time:
 // out[0..4] = F^n, out[5..9] = dF/dt. Returns false for a non-physical state.
 template <class T>
@@ -1152,18 +1270,14 @@ bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& r
         for (int a = 0; a < 3; ++a) xn[a] = (fc.xg[k][a] - fc.nb_to_owner.t[a]) / fc.nb_to_owner.s[a];
         T v0[5], g0[5][3];
         eval_recon(m, fc.nb, *rn, xn, v0, g0);
-        transform_state(fc.nb_to_owner, v0, vr);
+        transform_state(m, P, fc.nb_to_owner, v0, vr);
         for (int v = 0; v < 5; ++v) {
-          const double sv = (v >= 1 && v <= 3 && fc.nb_to_owner.s[v - 1] < 0) ? -1.0 : 1.0;
+          const double sv = (v >= 1 && v <= 3 && ((fc.nb_to_owner.vflip >> (v - 1)) & 1)) ? -1.0 : 1.0;
           for (int a = 0; a < 3; ++a) gr[v][a] = sv * fc.nb_to_owner.s[a] * g0[v][a];
         }
       } else {
-        // mirror image of the owner across the wall
-        transform_state(fc.nb_to_owner, vl, vr);
-        for (int v = 0; v < 5; ++v) {
-          const double sv = (v >= 1 && v <= 3 && fc.nb_to_owner.s[v - 1] < 0) ? -1.0 : 1.0;
-          for (int a = 0; a < 3; ++a) gr[v][a] = sv * fc.nb_to_owner.s[a] * gl[v][a];
-        }
+        // the wall's ghost at the Gauss point
+        wall_ghost(P, fc.wall_kind, fc.wall_plane, vl, gl, vr, gr);
       }
       // rotate into the local frame
       const double* n1 = fc.n[k];
@@ -1198,9 +1312,19 @@ bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& r
       }
     }
     if (fc.nb < 0) {
-      for (int s = 0; s < 2; ++s)
-        for (int v = 0; v < 5; ++v)
-          if (v != 1 + fc.wall_axis) acc[s][v] = T(0.0);
+      // walls are impermeable: no mass flux. A slip wall passes only normal momentum (its
+      // exact flux by symmetry); an adiabatic no-slip wall conducts no heat, so its energy flux
+      // is the work of the wall force, U_w . F_m; an isothermal wall keeps the GKS energy flux
+      for (int s = 0; s < 2; ++s) {
+        acc[s][0] = T(0.0);
+        if (fc.wall_kind == 1) {
+          for (int v = 1; v < 5; ++v)
+            if (v != 1 + fc.wall_axis) acc[s][v] = T(0.0);
+        } else if (P.Tw[fc.wall_plane] <= 0.0) {
+          const double* uw = P.uw[fc.wall_plane];
+          acc[s][4] = uw[0] * acc[s][1] + uw[1] * acc[s][2] + uw[2] * acc[s][3];
+        }
+      }
     }
     for (int v = 0; v < 5; ++v) {
       out[v] = (4.0 * acc[0][v] - acc[1][v]) / dt;
@@ -1284,11 +1408,29 @@ int step_implicit(const Mesh& m, const Params& P, double* Q, double dt, int nste
     const bool own = fc.owner == i;
     for (int c = 0; c < 3; ++c) nn[c] = own ? nrm[f][c] : -nrm[f][c];
     double q[5], dq[5];
-    if (fc.nb < 0) {  // mirror image of the cell
+    if (fc.nb < 0) {  // the wall's ghost of the cell: Q_p = G(Q_i), dQ_p = G(Q_i + dQ_i) - G(Q_i)
       get(X, i, q);
       get(dX, i, dq);
-      transform_state(fc.nb_to_owner, q, qp);
-      transform_state(fc.nb_to_owner, dq, dqp);
+      double zg[5][3] = {}, zgg[5][3];
+      wall_ghost(P, fc.wall_kind, fc.wall_plane, q, zg, qp, zgg);
+      // the slip and adiabatic maps are linear: dQ_p = G(dQ_i)
+      wall_ghost(P, fc.wall_kind, fc.wall_plane, dq, zg, dqp, zgg);
+      if (fc.wall_kind == 2 && P.Tw[fc.wall_plane] > 0.0) {
+        // isothermal: the change of |m|^2/rho written without cancellation,
+        // (2 m . dm + |dm|^2 - |m|^2 drho / rho) / (rho + drho)
+        const double r = q[0], dr = dq[0];
+        const double* uw = P.uw[fc.wall_plane];
+        double mdm = 0, dm2 = 0, m2 = 0, uwdm = 0;
+        for (int a = 0; a < 3; ++a) {
+          mdm += q[1 + a] * dq[1 + a];
+          dm2 += dq[1 + a] * dq[1 + a];
+          m2 += q[1 + a] * q[1 + a];
+          uwdm += uw[a] * dq[1 + a];
+        }
+        const double uw2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+        dqp[4] = (2.0 * P.Tw[fc.wall_plane] / (P.gamma - 1.0) + 2.0 * uw2) * dr - dq[4] +
+                 (2.0 * mdm + dm2 - m2 * dr / r) / (r + dr) - 2.0 * uwdm;
+      }
       return;
     }
     const int p = own ? fc.nb : fc.owner;
@@ -1525,6 +1667,18 @@ int oracle_gp_flux(const double* params, const double* ql, const double* dql, co
 
 void oracle_time_coeffs(double tau, double delta, double* c) { time_coeffs(tau, delta, c); }
 
+// Ghost value and gradient at a wall point (global frame), g and gg as [5][3].
+void oracle_wall_ghost(const double* params, int kind, int plane, const double* v,
+                       const double* g, double* vg, double* gg) {
+  const Params P = read_params(params);
+  double G[5][3], GG[5][3];
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) G[r][b] = g[3 * r + b];
+  wall_ghost(P, kind, plane, v, G, vg, GG);
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) gg[3 * r + b] = GG[r][b];
+}
+
 // Slope a (5) of <a psi> = b for a Maxwellian with primitive (U,V,W,lambda).
 void oracle_slope(double U, double V, double W, double lam, double K, const double* b, double* a) {
   slope(moments(U, V, W, lam, K, kFull), b, a);
@@ -1662,7 +1816,7 @@ int oracle_max_dt(void* h, const double* params, const double* Q, double cfl, do
     if (!primitive(q, P.gamma, w)) return ST_NONPHYS;
     const double speed = std::sqrt(w.U * w.U + w.V * w.V + w.W * w.W);
     const double cs = std::sqrt(P.gamma * w.p / w.rho);
-    const double nu = P.mu / w.rho;
+    const double nu = viscosity(P, w.p / w.rho) / w.rho;
     best = std::min(best, hi / (speed + cs + 2.0 * nu / hi));
   }
   *dt = cfl * best;
