@@ -45,14 +45,18 @@ typedef struct gks_solver gks_solver; /* opaque: device geometry, buffers, state
 
 /* Cell kinds: the value is the number of distinct vertices. */
 enum { GKS_TET = 4, GKS_PYR = 5, GKS_PRI = 6, GKS_HEX = 8 };
-/* Boundary condition per axis of the bounding box. */
-enum { GKS_BC_PERIODIC = 0, GKS_BC_REFLECT = 1 };
+/* Boundary condition per axis of the bounding box: periodic; slip (reflecting) walls; no-slip
+ * walls (Section 5: adiabatic or isothermal, possibly moving; their velocity and temperature are
+ * solver parameters, wall_u and wall_T below). */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_REFLECT = 1, GKS_BC_NOSLIP = 2 };
 /* Flux variants (Section 3.2): the smooth flux of Eq. flux-2 read as
  * g0 [1 - tau (a.u + A) + t A], or the full flux of Eq. flux-1. */
 enum { GKS_FLUX_SMOOTH = 0, GKS_FLUX_FULL = 1 };
 /* Collision time (Section 5): zero; inviscid tau = eps dt + C |pl-pr|/(pl+pr) dt;
- * viscous tau = mu/p + C |pl-pr|/(pl+pr) dt with p the interface pressure. */
-enum { GKS_TAU_ZERO = 0, GKS_TAU_INVISCID = 1, GKS_TAU_VISCOUS = 2 };
+ * viscous tau = mu/p + C |pl-pr|/(pl+pr) dt with p the interface pressure; viscous with the
+ * power law of Section 5.4, mu(T) = mu (T/T_ref)^mu_pow with T = p/rho of the interface
+ * equilibrium. */
+enum { GKS_TAU_ZERO = 0, GKS_TAU_INVISCID = 1, GKS_TAU_VISCOUS = 2, GKS_TAU_POWER_LAW = 3 };
 /* Arithmetic: FP64 everywhere, or FP32 reconstruction and flux with FP64 stencil
  * differences, FP64 face sums and FP64 update. */
 enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
@@ -72,10 +76,21 @@ typedef struct {
   double weno_eps;   /* epsilon of the nonlinear weights (not printed; default 1e-8) */
   int weno_pow;      /* exponent of tau/(beta+eps) in the nonlinear weights (printed: 1) */
   int precision;     /* GKS_PREC_* */
+  double T_ref;      /* GKS_TAU_POWER_LAW: reference temperature p/rho (> 0) */
+  double mu_pow;     /* GKS_TAU_POWER_LAW: exponent (Section 5.4: 0.7) */
+  /* No-slip walls, per plane axis + 3 side (side 1 the upper plane of the axis): velocity and
+   * temperature p/rho (<= 0: adiabatic). The ghost at a wall's Gauss points has the owner's
+   * density, U_g = 2 U_w - U and p_g = p (adiabatic) or T_g = 2 T_w - T (isothermal); ghost cells
+   * in the stencils take U_g = 2 U_w - U at the same density and pressure. The wall flux has no
+   * mass component; at an adiabatic wall its energy component is U_w . (momentum flux). Ignored
+   * on periodic and slip planes. The VJP supports adiabatic walls only. */
+  double wall_u[6][3];
+  double wall_T[6];
 } gks_params;
 
 /* Fill *p with the defaults above (gamma 1.4, Euler, smooth flux, zero collision time,
- * weno_gamma 0.0125, weno_eps 1e-8, weno_pow 1, FP64). */
+ * weno_gamma 0.0125, weno_eps 1e-8, weno_pow 1, FP64, T_ref 1, mu_pow 0.7, stationary
+ * adiabatic walls). */
 void gks_params_default(gks_params* p);
 
 /* Build the mesh topology on the host.
@@ -86,7 +101,8 @@ void gks_params_default(gks_params* p);
  *              prism {p1 p2 p3 p3 p4 p5 p6 p6}, hex {p1..p8}; the face labels F_p of Section 2
  *              (prism F3 read as {p1 p2 p5 p4}) fix the sub-stencils.
  *   bc, lo, hi the bounding box [lo, hi] and a condition per axis. Faces on a periodic axis
- *              match their translated image; unmatched faces must lie on a reflecting plane.
+ *              match their translated image; unmatched faces must lie on a wall plane (slip or
+ *              no-slip axis).
  * Builds faces, the big stencils S_i (face neighbours, then neighbours of neighbours, as a set
  * of (cell, periodic/mirror transform) pairs) and the sub-stencils of Section 2, and a
  * Morton reorder of cells used internally. Errors: GKS_E_INVAL (bad type/index),
@@ -188,8 +204,9 @@ gks_status gks_timing_read(gks_solver* s, double ms[3], int64_t counts[3]);
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]);
 
 /* Kernel launches in one pass of each hot kernel (0 reconstruction: one launch per range of
- * tiles of one cell kind; 1 face flux; 2 face sum + update), for counting the launches of a
- * timed region from the pass counts of gks_timing_read. */
+ * tiles of one cell kind, plus the ghost refresh when moving no-slip walls need ghost cells;
+ * 1 face flux; 2 face sum + update), for counting the launches of a timed region from the pass
+ * counts of gks_timing_read. */
 gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]);
 
 /* Algorithmic operation count of one face Gauss point of the flux kernel for a flux mode and

@@ -22,7 +22,8 @@ GKS_OK, GKS_E_INVAL, GKS_E_NOMEM, GKS_E_CUDA, GKS_E_MESH, GKS_E_SINGULAR, GKS_E_
 STATUS_NAMES = ["GKS_OK", "GKS_E_INVAL", "GKS_E_NOMEM", "GKS_E_CUDA", "GKS_E_MESH",
                 "GKS_E_SINGULAR", "GKS_E_NONPHYSICAL", "GKS_E_TIMEOUT"]
 GKS_FLUX_SMOOTH, GKS_FLUX_FULL = 0, 1
-GKS_TAU_ZERO, GKS_TAU_INVISCID, GKS_TAU_VISCOUS = 0, 1, 2
+GKS_TAU_ZERO, GKS_TAU_INVISCID, GKS_TAU_VISCOUS, GKS_TAU_POWER_LAW = 0, 1, 2, 3
+GKS_BC_PERIODIC, GKS_BC_REFLECT, GKS_BC_NOSLIP = 0, 1, 2
 GKS_PREC_FP64, GKS_PREC_MIXED = 0, 1
 
 
@@ -31,7 +32,9 @@ class gks_params(ctypes.Structure):
                 ("flux_mode", ctypes.c_int), ("tau_model", ctypes.c_int),
                 ("tau_eps", ctypes.c_double), ("tau_C", ctypes.c_double),
                 ("weno_gamma", ctypes.c_double), ("weno_eps", ctypes.c_double),
-                ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int),
+                ("T_ref", ctypes.c_double), ("mu_pow", ctypes.c_double),
+                ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6)]
 
 
 class GksError(RuntimeError):
@@ -97,6 +100,10 @@ def load_library(path: str = LIB_PATH):
     L.gks_cfl_dt_noalloc.restype = st
     for name in ("gks_gp_flux_host", "gks_gp_flux_vjp_host", "gks_gp_face_host"):
         getattr(L, name).restype = ctypes.c_int
+    L.gks_wall_ghost_host.argtypes = [P, ctypes.c_int] + [P] * 8
+    L.gks_wall_ghost_host.restype = None
+    L.gks_wall_flux_fix_host.argtypes = [P, ctypes.c_int, P]
+    L.gks_wall_flux_fix_host.restype = None
     L.gks_last_error.argtypes = [P]
     L.gks_last_error.restype = ctypes.c_char_p
     L.gks_destroy.argtypes = [P]
@@ -123,7 +130,17 @@ def gks_params_default(**overrides) -> gks_params:
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise KeyError(k)
-        setattr(p, k, v)
+        if k == "wall_u":
+            v = np.asarray(v, dtype=np.float64).reshape(6, 3)
+            for w in range(6):
+                for a in range(3):
+                    p.wall_u[w][a] = float(v[w, a])
+        elif k == "wall_T":
+            v = np.asarray(v, dtype=np.float64).reshape(6)
+            for w in range(6):
+                p.wall_T[w] = float(v[w])
+        else:
+            setattr(p, k, v)
     return p
 
 

@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
     int64_t nf, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const double* __restrict__ fgp,
     const double* __restrict__ poly, const double* __restrict__ gL, const double* __restrict__ gLt,
-    const double* __restrict__ vol, int64_t nc, FluxParams<double> P, double dt,
-    double* __restrict__ gpf, int* flag) {
+    const double* __restrict__ vol, int64_t nc, FluxParams<double> P,
+    const double* __restrict__ wall_tab, double dt, double* __restrict__ gpf, int* flag) {
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t f = gid >> 2;
   const bool active = f < nf;
@@ -58,9 +58,7 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
         gacc[5 + q] += gLt[q * nc + nb] * in;
       }
     } else {
-#pragma unroll
-      for (int q = 0; q < 5; ++q)
-        if (q != 1 + wall) gacc[q] = gacc[5 + q] = 0.0;  // zeroed wall components
+      wall_flux_fix_adj(wall, wall_data(wall_tab, wall), gacc);  // the wall treatment, reversed
     }
     double dl[3], dr[3], n1[3];
 #pragma unroll
@@ -75,13 +73,7 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
     if (nb >= 0) {
       eval_poly(PolyRef64{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
     } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const double sv = (v == 1 + wall) ? -1.0 : 1.0;
-        vr[v] = sv * vl[v];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gr[v][a] = (a == wall ? -sv : sv) * gl[v][a];
-      }
+      wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
     }
     double gvl[5] = {0, 0, 0, 0, 0}, gvr[5] = {0, 0, 0, 0, 0};
     double ggl[5][3], ggr[5][3];
@@ -90,16 +82,8 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
 #pragma unroll
       for (int a = 0; a < 3; ++a) ggl[v][a] = ggr[v][a] = 0.0;
     if (gp_flux_global_vjp(P, vl, gl, vr, gr, n1, w, dt, gacc, gvl, ggl, gvr, ggr)) {
-      if (nb < 0) {
-        // the mirror state is a function of the owner's: fold its cotangent back
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          const double sv = (v == 1 + wall) ? -1.0 : 1.0;
-          gvl[v] += sv * gvr[v];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) ggl[v][a] += (a == wall ? -sv : sv) * ggr[v][a];
-        }
-      }
+      // the wall's ghost is a function of the owner's value and gradient: fold its cotangent back
+      if (nb < 0) wall_ghost_vjp(P, wall, wall_data(wall_tab, wall), vl, gl, gvr, ggr, gvl, ggl);
       eval_poly_adj(dl, gvl, ggl, go);
       if (nb >= 0) eval_poly_adj(dr, gvr, ggr, gn);
     } else {
@@ -336,19 +320,31 @@ __global__ void __launch_bounds__(64) k_vjp_recon(
 
 __global__ void k_vjp_stencil(int64_t nc, const int32_t* __restrict__ rs_ptr,
                               const int32_t* __restrict__ rs_pos, const int32_t* __restrict__ t_idx,
-                              const double* __restrict__ gdq, const double* __restrict__ gq0,
-                              double* __restrict__ gQ) {
+                              const double* __restrict__ g_map, const double* __restrict__ gdq,
+                              const double* __restrict__ gq0, double* __restrict__ gQ) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= nc) return;
   double s[5];
   for (int v = 0; v < 5; ++v) s[v] = gq0[v * nc + j];
   for (int k = rs_ptr[j]; k < rs_ptr[j + 1]; ++k) {
     const int64_t pos = rs_pos[k];
-    const int fl = t_idx[pos] >> kFlipShift;
+    const int32_t e = t_idx[pos];
+    const int fl = e >> kFlipShift;
     const int64_t slot = pos / kTile, lane = pos % kTile;
     const double* g = gdq + slot * 5 * kTile + lane;
+    double y[5];
+    for (int v = 0; v < 5; ++v) y[v] = g[v * kTile];
+    if ((e & kCellMask) >= nc) {
+      // a wall ghost slot: the transpose of its map (rho, m_j, E) -> (rho, s_j m_j + a_j rho,
+      // E + b rho + c . m)
+      const double* c = g_map + 10 * ((e & kCellMask) - nc);
+      s[0] += y[0] + c[3] * y[1] + c[4] * y[2] + c[5] * y[3] + c[6] * y[4];
+      for (int a = 0; a < 3; ++a) s[1 + a] += c[a] * y[1 + a] + c[7 + a] * y[4];
+      s[4] += y[4];
+      continue;
+    }
     for (int v = 0; v < 5; ++v) {
-      double x = g[v * kTile];
+      double x = y[v];
       if (v >= 1 && v <= 3 && ((fl >> (v - 1)) & 1)) x = -x;
       s[v] += x;
     }
@@ -362,23 +358,17 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
                 const double* QA, const double* poly, const double* gL, const double* gLt,
                 double dt, double* gpf, double* gpc, double* gdq, double* gq0, double* gQ,
                 const int32_t* rs_ptr, const int32_t* rs_pos, int* flag, cudaStream_t st) {
-  FluxParams<double> fp;
-  fp.gamma = p.gamma;
-  fp.K = p.K;
-  fp.mu = p.mu;
-  fp.tau_eps = p.tau_eps;
-  fp.tau_C = p.tau_C;
-  fp.full = p.flux_mode;
-  fp.tau_model = p.tau_model;
+  const FluxParams<double> fp = flux_params(p);
   k_vjp_flux<<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.f_owner, m.f_nb, m.f_wall, g.fgp,
-                                                          poly, gL, gLt, g64.vol, m.nc, fp, dt, gpf,
-                                                          flag);
+                                                          poly, gL, gLt, g64.vol, m.nc, fp,
+                                                          m.wall64, dt, gpf, flag);
   k_vjp_poly<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, gpf, gpc);
   k_vjp_recon<<<blocks_for(m.nc, 64), 64, 0, st>>>(m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
                                                      m.t_idx, m.st_ptr, m.n_sub, g.Ap, g.Bp, g.mom,
                                                      g.h, p.weno_gamma, p.weno_eps, p.weno_pow, gpc,
                                                      gdq, gq0);
-  k_vjp_stencil<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, rs_ptr, rs_pos, m.t_idx, gdq, gq0, gQ);
+  k_vjp_stencil<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, rs_ptr, rs_pos, m.t_idx, m.g_map,
+                                                        gdq, gq0, gQ);
 }
 
 }  // namespace gks

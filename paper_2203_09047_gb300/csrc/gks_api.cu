@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -150,6 +151,8 @@ KParams<R> kparams(const gks_params& p) {
   k.weno_gamma = (R)p.weno_gamma;
   k.weno_eps = (R)p.weno_eps;
   k.weno_pow = p.weno_pow;
+  k.T_ref = (R)p.T_ref;
+  k.mu_pow = (R)p.mu_pow;
   return k;
 }
 
@@ -177,8 +180,9 @@ gks_status alloc_geo(gks_solver* s, GeoR<R>& g) {
   R* qsa = nullptr;
   if ((e = salloc(s, &poly, (int64_t)kPolyStride * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc poly");
   if ((e = salloc(s, &ff, (int64_t)kFaceStride * nf)) != cudaSuccess) return s->cuda_fail(e, "alloc face flux");
-  if ((e = salloc(s, &qa, (int64_t)Lay<R>::gq * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
-  if ((e = salloc(s, &qsa, (int64_t)Lay<R>::gq * nc)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
+  const int64_t nq = nc + s->m.ng;  // cells and wall ghost slots
+  if ((e = salloc(s, &qa, (int64_t)Lay<R>::gq * nq)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
+  if ((e = salloc(s, &qsa, (int64_t)Lay<R>::gq * nq)) != cudaSuccess) return s->cuda_fail(e, "alloc gather copy");
   s->poly = poly;
   s->fface = ff;
   s->QA = qa;
@@ -264,6 +268,103 @@ gks_status check_and_clear(gks_solver* s) {
   return GKS_OK;
 }
 
+// Ghost slots of moving no-slip walls (DevMesh::ng). The flow variables of a stencil image are
+// the wall maps of the planes it was reflected across, applied in order (Section 2: ghost
+// variables from the boundary condition): slip, m_axis -> -m_axis; no-slip with velocity U_w,
+// rho -> rho, m -> 2 U_w rho - m, E -> E + 2 |U_w|^2 rho - 2 U_w . m (same density and
+// pressure). The composition is kept as rho -> rho, m_j -> s_j m_j + a_j rho,
+// E -> E + b rho + c . m. Entries whose map is a pure sign change keep their flip bits; the
+// others point at a ghost slot nc + g (one per source cell and plane sequence).
+struct WallMap {
+  double s[3] = {1, 1, 1}, a[3] = {0, 0, 0}, b = 0, c[3] = {0, 0, 0};
+};
+WallMap wall_map_of(const HostMesh& h, const gks_params& p, uint8_t code) {
+  WallMap M;
+  for (int k = 0; k < 2; ++k) {
+    const int w = ((code >> (3 * k)) & 7) - 1;
+    if (w < 0) break;
+    const int ax = w % 3;
+    WallMap W;
+    if (h.bc[ax] == GKS_BC_REFLECT) {
+      W.s[ax] = -1;
+    } else {
+      const double* uw = p.wall_u[w];
+      W.s[0] = W.s[1] = W.s[2] = -1;
+      W.b = 2.0 * (uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2]);
+      for (int j = 0; j < 3; ++j) {
+        W.a[j] = 2.0 * uw[j];
+        W.c[j] = -2.0 * uw[j];
+      }
+    }
+    WallMap C;  // W after M
+    C.b = M.b + W.b;
+    for (int j = 0; j < 3; ++j) {
+      C.s[j] = W.s[j] * M.s[j];
+      C.a[j] = W.s[j] * M.a[j] + W.a[j];
+      C.c[j] = M.c[j] + M.s[j] * W.c[j];
+      C.b += W.c[j] * M.a[j];
+    }
+    M = C;
+  }
+  return M;
+}
+bool wall_map_is_signs(const WallMap& M) {
+  if (M.b != 0.0) return false;
+  for (int j = 0; j < 3; ++j)
+    if (M.a[j] != 0.0 || M.c[j] != 0.0) return false;
+  return true;
+}
+// Patches the tile entries (t_idx) and fills the ghost tables; false if the slots do not fit
+// the entry's cell field.
+bool build_wall_ghosts(const HostMesh& h, const gks_params& p, std::vector<int32_t>& tidx,
+                       std::vector<int32_t>& gsrc, std::vector<double>& gmap,
+                       std::vector<float>& gmapf) {
+  tidx = h.t_idx;
+  gsrc.clear();
+  gmap.clear();
+  gmapf.clear();
+  bool any = false;
+  for (int a = 0; a < 3; ++a) any = any || h.bc[a] == GKS_BC_NOSLIP;
+  if (!any) return true;
+  const int64_t nc = h.n_cells;
+  std::map<int64_t, int32_t> slot_of;  // (src << 8 | plane code) -> slot
+  for (int64_t t = 0; t < h.n_tiles; ++t)
+    for (int l = 0; l < kTile; ++l) {
+      const int64_t c = t * kTile + l;
+      if (c >= nc) continue;
+      const int Kc = h.st_ptr[c + 1] - h.st_ptr[c];
+      for (int k = 0; k < Kc; ++k) {
+        const int64_t e = h.st_ptr[c] + k;
+        const uint8_t code = h.st_walls[e];
+        if (!code) continue;
+        const WallMap M = wall_map_of(h, p, code);
+        if (wall_map_is_signs(M)) continue;
+        const int32_t src = h.st_idx[e] & kCellMask;
+        const int64_t key = ((int64_t)src << 8) | code;
+        auto it = slot_of.find(key);
+        int32_t g;
+        if (it == slot_of.end()) {
+          g = (int32_t)gsrc.size();
+          slot_of.emplace(key, g);
+          gsrc.push_back(src);
+          const double v[10] = {M.s[0], M.s[1], M.s[2], M.a[0], M.a[1], M.a[2], M.b,
+                                M.c[0], M.c[1], M.c[2]};
+          for (double x : v) {
+            gmap.push_back(x);
+            const float hi = (float)x;
+            gmapf.push_back(hi);
+            gmapf.push_back((float)(x - (double)hi));
+          }
+        } else {
+          g = it->second;
+        }
+        if (nc + g > (int64_t)kCellMask) return false;
+        tidx[((size_t)h.t_st[t] + k) * kTile + l] = (int32_t)(nc + g);
+      }
+    }
+  return true;
+}
+
 bool valid_params(const gks_params* p, std::string& why) {
   if (!(p->gamma > 1.0 && p->gamma < 5.0 / 3.0 + 1e-12)) { why = "gamma must lie in (1, 5/3]"; return false; }
   if (!(p->mu >= 0.0)) { why = "mu must be >= 0"; return false; }
@@ -273,7 +374,17 @@ bool valid_params(const gks_params* p, std::string& why) {
     return false;
   }
   if (p->flux_mode != GKS_FLUX_SMOOTH && p->flux_mode != GKS_FLUX_FULL) { why = "flux_mode"; return false; }
-  if (p->tau_model < GKS_TAU_ZERO || p->tau_model > GKS_TAU_VISCOUS) { why = "tau_model"; return false; }
+  if (p->tau_model < GKS_TAU_ZERO || p->tau_model > GKS_TAU_POWER_LAW) { why = "tau_model"; return false; }
+  if (p->tau_model == GKS_TAU_POWER_LAW && !(p->T_ref > 0.0 && std::isfinite(p->mu_pow))) {
+    why = "the power law needs T_ref > 0 and a finite exponent";
+    return false;
+  }
+  for (int w = 0; w < 6; ++w)
+    if (!(std::isfinite(p->wall_u[w][0]) && std::isfinite(p->wall_u[w][1]) &&
+          std::isfinite(p->wall_u[w][2]) && std::isfinite(p->wall_T[w]))) {
+      why = "wall velocity and temperature must be finite";
+      return false;
+    }
   if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
   if (!(p->weno_eps > 0.0)) { why = "weno_eps must be > 0"; return false; }
   if (p->weno_pow < 1 || p->weno_pow > 4) { why = "weno_pow must be 1..4"; return false; }
@@ -311,12 +422,12 @@ gks_status step_implicit_r(gks_solver* s, GeoR<R>& g, double dt, int nsteps, int
     s->tock(t);
     t = s->tick(2);
     launch_jacobi_init<R>(s->m, (const R*)s->fface, (const R*)s->jfn, s->g.vol, dt,
-                          (const R*)s->QA, (R*)s->jR, (R*)s->jD, (R*)s->jhrs, dq[0],
-                          s->prm.gamma, s->st);
+                          (const R*)s->QA, (R*)s->jR, (R*)s->jD, (R*)s->jhrs, dq[0], kp,
+                          s->st);
     for (int it = 1; it <= kmax; ++it)
       launch_jacobi_sweep<R>(s->m, (const R*)s->jfn, (const R*)s->QA, (const R*)s->jR,
                              (const R*)s->jD, (const R*)s->jhrs, dq[(it - 1) & 1], dq[it & 1],
-                             it == kmax, (R*)s->QsA, s->prm.gamma, s->flag, s->st);
+                             it == kmax, (R*)s->QsA, kp, s->flag, s->st);
     s->tock(t);
     std::swap(s->QA, s->QsA);  // Q^{n+1} was written to the other gather copy
   }
@@ -342,6 +453,12 @@ void gks_params_default(gks_params* p) {
   p->weno_eps = 1e-8;
   p->weno_pow = 1;
   p->precision = GKS_PREC_FP64;
+  p->T_ref = 1.0;
+  p->mu_pow = 0.7;
+  for (int w = 0; w < 6; ++w) {
+    p->wall_u[w][0] = p->wall_u[w][1] = p->wall_u[w][2] = 0.0;
+    p->wall_T[w] = 0.0;
+  }
 }
 
 gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
@@ -433,7 +550,32 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if ((e = supload(s, &m.t_cnt, h.t_cnt)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_st, h.t_st)) != cudaSuccess) return bad("upload");
   if ((e = supload(s, &m.t_sb, h.t_sb)) != cudaSuccess) return bad("upload");
-  if ((e = supload(s, &m.t_idx, h.t_idx)) != cudaSuccess) return bad("upload");
+  {
+    std::vector<int32_t> tidx, gsrc;
+    std::vector<double> gmap;
+    std::vector<float> gmapf;
+    if (!build_wall_ghosts(h, *p, tidx, gsrc, gmap, gmapf)) {
+      g_mesh_err = "too many wall ghost cells for the stencil entry format";
+      gks_destroy(s);
+      return GKS_E_MESH;
+    }
+    if ((e = supload(s, &m.t_idx, tidx)) != cudaSuccess) return bad("upload");
+    std::vector<double> w64(24);
+    std::vector<float> w32(24);
+    for (int w = 0; w < 6; ++w) {
+      for (int a = 0; a < 3; ++a) w64[4 * w + a] = p->wall_u[w][a];
+      w64[4 * w + 3] = p->wall_T[w];
+    }
+    for (int k = 0; k < 24; ++k) w32[k] = (float)w64[k];
+    if ((e = supload(s, &m.wall64, w64)) != cudaSuccess) return bad("upload");
+    if ((e = supload(s, &m.wall32, w32)) != cudaSuccess) return bad("upload");
+    m.ng = (int64_t)gsrc.size();
+    if (m.ng > 0) {
+      if ((e = supload(s, &m.g_src, gsrc)) != cudaSuccess) return bad("upload");
+      if ((e = supload(s, &m.g_map, gmap)) != cudaSuccess) return bad("upload");
+      if ((e = supload(s, &m.g_mapf, gmapf)) != cudaSuccess) return bad("upload");
+    }
+  }
   // tile ranges by the kind of each tile's first cell (at most one per kind: cells are ordered
   // by kind first); a new range is opened only while slots remain, else the last one grows
   for (int64_t t = 0; t < h.n_tiles; ++t) {
@@ -550,7 +692,9 @@ gks_status gks_max_dt(gks_solver* s, double cfl, double* dt) {
   sync_q(s);
   launch_check_state(s->m.nc, s->Q, s->prm.gamma, s->flag, s->st);
   const int nb = dt_blocks(s->m.nc);
-  launch_dt(s->m.nc, s->Q, s->g.hdt, s->prm.gamma, s->prm.mu, s->dt_part, nb, s->dt_out, s->st);
+  launch_dt(s->m.nc, s->Q, s->g.hdt, s->prm.gamma, s->prm.mu,
+            s->prm.tau_model == GKS_TAU_POWER_LAW, s->prm.T_ref, s->prm.mu_pow, s->dt_part, nb,
+            s->dt_out, s->st);
   gks_status r = check_and_clear(s);
   if (r != GKS_OK) return r;
   cudaError_t e = cudaMemcpyAsync(s->h_dt, s->dt_out, sizeof(double), cudaMemcpyDeviceToHost, s->st);
@@ -619,7 +763,7 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
       s->gv = s->gd;
     }
     if ((e = salloc(s, &s->vQ, 5 * nc)) != cudaSuccess ||
-        (e = salloc(s, &s->vQA, 6 * nc)) != cudaSuccess ||
+        (e = salloc(s, &s->vQA, 6 * (nc + s->m.ng))) != cudaSuccess ||
         (e = salloc(s, &s->vpoly, (int64_t)kPolyStride * nc)) != cudaSuccess ||
         (e = salloc(s, &s->vgL, 5 * nc)) != cudaSuccess ||
         (e = salloc(s, &s->vgLt, 5 * nc)) != cudaSuccess ||
@@ -698,6 +842,7 @@ gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]) {
   if (!s || !launches) return GKS_E_INVAL;
   launches[0] = 0;
   for (int r = 0; r < s->m.rr.n; ++r) launches[0] += s->m.rr.t1[r] > s->m.rr.t0[r] ? 1 : 0;
+  if (s->m.ng > 0) launches[0] += 1;  // the ghost refresh of moving no-slip walls
   launches[1] = 1;
   launches[2] = 1;
   return GKS_OK;

@@ -81,7 +81,26 @@ struct DevMesh {
   int32_t* t_sb = nullptr;
   int32_t* t_idx = nullptr;
   TileRanges rr;
+  // ghost cells of moving no-slip walls: stencil entries whose image's flow variables are not a
+  // sign change of the source cell's (Section 2: ghost variables from the boundary condition)
+  // point at slot nc + g of the gather copies, refreshed before each reconstruction from cell
+  // g_src[g] by the linear map g_map[g] = (s[3], a[3], b, c[3]):
+  //   rho -> rho, m_j -> s_j m_j + a_j rho, E -> E + b rho + c . m
+  // (g_mapf: the same ten values as float-float pairs for the FP32 path).
+  int64_t ng = 0;
+  int32_t* g_src = nullptr;
+  double* g_map = nullptr;
+  float* g_mapf = nullptr;
+  // no-slip wall planes (axis + 3 side): velocity and temperature, [6][4] in FP64 and FP32
+  double* wall64 = nullptr;
+  float* wall32 = nullptr;
 };
+template <class R>
+inline const R* wall_table(const DevMesh& m);
+template <>
+inline const double* wall_table<double>(const DevMesh& m) { return m.wall64; }
+template <>
+inline const float* wall_table<float>(const DevMesh& m) { return m.wall32; }
 
 // FP64 geometry (always kept).
 struct Geo64 {
@@ -112,6 +131,7 @@ struct KParams {
   int flux_mode, tau_model;
   R weno_gamma, weno_eps;
   int weno_pow;
+  R T_ref, mu_pow;  // power-law viscosity (the wall planes live in DevMesh::wall64/wall32)
 };
 
 // ---- precompute (gks_geom.cu) -------------------------------------------------------------
@@ -163,12 +183,12 @@ void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage,
 // [5][nc], D [nc], hrs [cf entries]; fn is [nf][4] from launch_face_normals.
 template <class R>
 void launch_jacobi_init(const DevMesh& m, const R* fface, const R* fn, const double* vol,
-                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0, double gamma,
+                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0, const KParams<R>& kp,
                         cudaStream_t st);
 template <class R>
 void launch_jacobi_sweep(const DevMesh& m, const R* fn, const R* QA, const R* Rv, const R* D,
-                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout, double gamma,
-                         int* flag, cudaStream_t st);
+                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout,
+                         const KParams<R>& kp, int* flag, cudaStream_t st);
 
 // The state [5][nc] in FP64 (internal order) from its gather copy.
 template <class R>
@@ -179,8 +199,9 @@ void launch_permute_in(int64_t nc, const int32_t* perm, const double* src, doubl
 void launch_permute_out(int64_t nc, const int32_t* perm, const double* src, double* dst,
                         cudaStream_t st);
 void launch_check_state(int64_t nc, const double* Q, double gamma, int* flag, cudaStream_t st);
-void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, double mu,
-               double* partial, int nblocks, double* out, cudaStream_t st);
+void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, double mu, int power,
+               double T_ref, double mu_pow, double* partial, int nblocks, double* out,
+               cudaStream_t st);
 int dt_blocks(int64_t nc);
 
 // ---- adjoint (gks_adjoint.cu) --------------------------------------------------------------

@@ -7,7 +7,8 @@
 
 namespace {
 gks::FluxParams<double> params_from(const double* p) {
-  // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr}
+  // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr, T_ref, mu_pow,
+  //      wall_u[6][3], wall_T[6]}
   gks::FluxParams<double> P;
   P.gamma = p[0];
   P.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
@@ -17,7 +18,19 @@ gks::FluxParams<double> params_from(const double* p) {
   P.full = (int)p[4];
   P.tau_model = (int)p[5];
   P.pr_fix = 1.0 / p[6] - 1.0;
+  P.T_ref = p[7];
+  P.mu_pow = p[8];
   return P;
+}
+// the wall plane of `code` from p's wall_u[6][3], wall_T[6]
+gks::WallData<double> wall_from(const double* p, int code) {
+  gks::WallData<double> d;
+  if (code >= 6) {
+    const int w = code - 6;
+    for (int a = 0; a < 3; ++a) d.uw[a] = p[9 + 3 * w + a];
+    d.Tw = p[27 + w];
+  }
+  return d;
 }
 }  // namespace
 
@@ -82,4 +95,33 @@ extern "C" int gks_gp_face_host(const double* p, const double* vl, const double*
       ggr[3 * v + a] = gGR[v][a];
     }
   return 0;
+}
+
+// The wall ghost at a Gauss point (value, gradient [5][3]) for wall code `code`, and, when gvg is
+// given, the reverse pass: (gvg, ggg) -> (gv, gg) (overwritten).
+extern "C" void gks_wall_ghost_host(const double* p, int code, const double* v, const double* g,
+                                    double* vg, double* gg, const double* gvg, const double* ggg,
+                                    double* gv, double* gga) {
+  const gks::FluxParams<double> P = params_from(p);
+  double G[5][3], GG[5][3];
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) G[r][b] = g[3 * r + b];
+  const gks::WallData<double> wd = wall_from(p, code);
+  gks::wall_ghost(P, code, wd, v, G, vg, GG);
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) gg[3 * r + b] = GG[r][b];
+  if (!gvg) return;
+  double Y[5][3], A[5][3] = {};
+  for (int r = 0; r < 5; ++r) {
+    gv[r] = 0.0;
+    for (int b = 0; b < 3; ++b) Y[r][b] = ggg[3 * r + b];
+  }
+  gks::wall_ghost_vjp(P, code, wd, v, G, gvg, Y, gv, A);
+  for (int r = 0; r < 5; ++r)
+    for (int b = 0; b < 3; ++b) gga[3 * r + b] = A[r][b];
+}
+
+// The wall treatment of a face's summed flux acc[10] (in place).
+extern "C" void gks_wall_flux_fix_host(const double* p, int code, double* acc) {
+  gks::wall_flux_fix(code, wall_from(p, code), acc);
 }

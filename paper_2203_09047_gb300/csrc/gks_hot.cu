@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fgp, const R* __restrict__ poly,
-    FluxParams<R> P, R dt, R* __restrict__ fface, int* flag) {
+    FluxParams<R> P, const R* __restrict__ wall_tab, R dt, R* __restrict__ fface, int* flag) {
   P.full = kFull;
   if (kTau0) P.tau_model = 0;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -480,14 +480,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     if (nb >= 0) {
       eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
     } else {
-      // mirror image of the owner across the wall plane (axis `wall`)
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const R sv = (v == 1 + wall) ? R(-1) : R(1);
-        vr[v] = sv * vl[v];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gr[v][a] = (a == wall ? -sv : sv) * gl[v][a];
-      }
+      wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);  // the wall's ghost
     }
     if (!gp_flux_global(P, vl, gl, vr, gr, n1, w, dt, acc)) atomicOr(flag, kErrNonphysical);
   }
@@ -498,12 +491,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
   }
   if (active && (gid & 3) == 0) {
-    if (wall >= 0) {
-      // reflecting wall: only the normal momentum component survives
-#pragma unroll
-      for (int v = 0; v < 5; ++v)
-        if (v != 1 + wall) acc[v] = acc[5 + v] = R(0);
-    }
+    if (wall >= 0) wall_flux_fix(wall, wall_data(wall_tab, wall), acc);
     R* o = fface + (int64_t)kFaceStride * f;
 #pragma unroll
     for (int q = 0; q < 10; ++q) o[q] = acc[q];
@@ -725,8 +713,43 @@ __device__ __forceinline__ void euler_flux_change(const R q[5], const R d[5], co
   out[4] = (d[4] + dp) * un1 + (q[4] + p) * dun;
 }
 
-// The other side of cell-face entry e seen from cell i: its index (-1: mirror image across wall
-// axis *wall) and the unit normal out of cell i with the face area.
+// The wall's ghost of a cell state q and of an increment d of it: q_g = G(q), d_g = G(q + d) -
+// G(q), with G the value part of wall_ghost. The slip and adiabatic maps are linear, so
+// d_g = G(d); the isothermal map's energy row holds |m|^2 / rho, whose change is formed as
+// (2 m . dm + |dm|^2 - |m|^2 drho / rho) / (rho + drho) without cancellation.
+template <class R>
+__device__ __forceinline__ void wall_cell_ghost(const FluxParams<R>& P, int code,
+                                                const WallData<R>& wd, const R q[5], R qg[5]) {
+  const R zg[5][3] = {};
+  R gg[5][3];
+  wall_ghost(P, code, wd, q, zg, qg, gg);
+}
+template <class R>
+__device__ __forceinline__ void wall_cell_ghost_inc(const FluxParams<R>& P, int code,
+                                                    const WallData<R>& wd, const R q[5],
+                                                    const R d[5], R dg[5]) {
+  const R zg[5][3] = {};
+  R gg[5][3];
+  if (code < 6 || wd.Tw <= R(0)) {
+    wall_ghost(P, code, wd, d, zg, dg, gg);
+    return;
+  }
+  const R u0 = wd.uw[0], u1 = wd.uw[1], u2 = wd.uw[2];
+  const R uw2 = u0 * u0 + u1 * u1 + u2 * u2;
+  dg[0] = d[0];
+  dg[1] = R(2) * u0 * d[0] - d[1];
+  dg[2] = R(2) * u1 * d[0] - d[2];
+  dg[3] = R(2) * u2 * d[0] - d[3];
+  const R mdm = q[1] * d[1] + q[2] * d[2] + q[3] * d[3];
+  const R dm2 = d[1] * d[1] + d[2] * d[2] + d[3] * d[3];
+  const R m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  dg[4] = (R(2) * wd.Tw / (P.gamma - R(1)) + R(2) * uw2) * d[0] - d[4] +
+          (R(2) * mdm + dm2 - m2 * d[0] / q[0]) / (q[0] + d[0]) -
+          R(2) * (u0 * d[1] + u1 * d[2] + u2 * d[3]);
+}
+
+// The other side of cell-face entry e seen from cell i: its index (-1: the wall's ghost of cell
+// i, *wall the wall code) and the unit normal out of cell i with the face area.
 template <class R>
 __device__ __forceinline__ int64_t other_side(int32_t e, const int32_t* __restrict__ f_owner,
                                               const int32_t* __restrict__ f_nb,
@@ -748,8 +771,10 @@ __global__ void __launch_bounds__(256) k_jacobi_init(
     int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
     const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fface, const R* __restrict__ fn,
-    const double* __restrict__ vol, double dt, const R* __restrict__ QA, R gm1, R* __restrict__ Rv,
-    R* __restrict__ D, R* __restrict__ hrs, R* __restrict__ dQ0) {
+    const double* __restrict__ vol, double dt, const R* __restrict__ QA, FluxParams<R> P,
+    const R* __restrict__ wall_tab, R* __restrict__ Rv, R* __restrict__ D, R* __restrict__ hrs,
+    R* __restrict__ dQ0) {
+  const R gm1 = P.gamma - R(1);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
   R qi[5];
@@ -763,11 +788,7 @@ __global__ void __launch_bounds__(256) k_jacobi_init(
     if (p >= 0) {
       state_of(QA, p, qp);
     } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) qp[v] = qi[v];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (a == wall) qp[1 + a] = -qp[1 + a];
+      wall_cell_ghost(P, wall, wall_data(wall_tab, wall), qi, qp);
     }
     const R r = fmax(wave_speed(qi, n, gm1), wave_speed(qp, n, gm1));
     hrs[k] = R(0.5) * r * S;
@@ -805,9 +826,11 @@ __global__ void __launch_bounds__(256) k_jacobi_sweep(
     const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fn, const R* __restrict__ QA,
     const R* __restrict__ Rv, const R* __restrict__ D, const R* __restrict__ hrs,
-    const R* __restrict__ dQin, R* __restrict__ dQout, R* __restrict__ QAout, R gm1, int* flag) {
+    const R* __restrict__ dQin, R* __restrict__ dQout, R* __restrict__ QAout, FluxParams<R> P,
+    const R* __restrict__ wall_tab, int* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nc) return;
+  const R gm1 = P.gamma - R(1);
   R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
   const int k0 = cf_ptr[i], k1 = cf_ptr[i + 1];
   for (int k = k0; k < k1; ++k) {
@@ -818,13 +841,16 @@ __global__ void __launch_bounds__(256) k_jacobi_sweep(
     state_of(QA, c, qp);
 #pragma unroll
     for (int v = 0; v < 5; ++v) dp[v] = dQin[v * nc + c];
-    if (p < 0) {  // mirror image of the cell
+    if (p < 0) {  // the wall's ghost of the cell and of its increment
+      R qg[5], dg[5];
+      const WallData<R> wd = wall_data(wall_tab, wall);
+      wall_cell_ghost(P, wall, wd, qp, qg);
+      wall_cell_ghost_inc(P, wall, wd, qp, dp, dg);
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (a == wall) {
-          qp[1 + a] = -qp[1 + a];
-          dp[1 + a] = -dp[1 + a];
-        }
+      for (int v = 0; v < 5; ++v) {
+        qp[v] = qg[v];
+        dp[v] = dg[v];
+      }
     }
     euler_flux_change(qp, dp, n, gm1, dT);
     const R h = hrs[k];
@@ -907,7 +933,8 @@ constexpr int kDtMaxBlocks = 1024;
 
 __global__ void __launch_bounds__(kDtThreads) k_dt_partial(int64_t nc, const double* __restrict__ Q,
                                                            const double* __restrict__ hdt,
-                                                           double gamma, double mu,
+                                                           double gamma, double mu, int power,
+                                                           double T_ref, double mu_pow,
                                                            double* partial) {
   __shared__ double red[kDtThreads / 32];
   double best = DBL_MAX;
@@ -918,7 +945,9 @@ __global__ void __launch_bounds__(kDtThreads) k_dt_partial(int64_t nc, const dou
     const double p = (gamma - 1.0) * (E - 0.5 * r * u2);
     const double c = sqrt(gamma * p / r);
     const double h = hdt[i];
-    const double bound = h / (sqrt(u2) + c + 2.0 * mu / (r * h));
+    // viscosity at the cell's temperature p / rho (the power law of Section 5.4, else constant)
+    const double mue = power ? mu * pow(p / (r * T_ref), mu_pow) : mu;
+    const double bound = h / (sqrt(u2) + c + 2.0 * mue / (r * h));
     best = fmin(best, bound);  // NaN states are caught by the state checks
   }
   for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -959,12 +988,55 @@ void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p,
       m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag);
 }
 
+// Ghost slots of moving no-slip walls: QA[nc + g] = map g applied to QA[g_src[g]].
+template <class R>
+__global__ void __launch_bounds__(128) k_ghost_fill(int64_t nc, int64_t ng,
+                                                    const int32_t* __restrict__ src,
+                                                    const double* __restrict__ map,
+                                                    const float* __restrict__ mapf, R* QA) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= ng) return;
+  Gq<R> g;
+  g.load(QA, src[k]);
+  if constexpr (std::is_same<R, float>::value) {
+    const float* c = mapf + 20 * k;
+    auto co = [&](int j) { return ff{c[2 * j], c[2 * j + 1]}; };
+    ff q[5], o[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = ff{g.hi[v], g.lo[v]};
+    o[0] = q[0];
+    o[4] = ff_add(q[4], ff_mul(co(6), q[0]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float sj = c[2 * j];  // +-1, exact
+      o[1 + j] = ff_add(ff{sj * q[1 + j].h, sj * q[1 + j].l}, ff_mul(co(3 + j), q[0]));
+      o[4] = ff_add(o[4], ff_mul(co(7 + j), q[1 + j]));
+    }
+    Gq<float>::store_ff(QA, nc + k, o);
+  } else {
+    const double* c = map + 10 * k;
+    double o[5];
+    o[0] = g.q[0];
+    o[4] = g.q[4] + c[6] * g.q[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      o[1 + j] = c[j] * g.q[1 + j] + c[3 + j] * g.q[0];
+      o[4] += c[7 + j] * g.q[1 + j];
+    }
+    Gq<double>::store(QA, nc + k, o);
+  }
+}
+
 // One launch per tile range, the bulk-copy variant whenever its shared memory fits a block. The
 // ranges are independent: with fj, range r > 0 runs on auxiliary stream r - 1, forked from and
 // joined back into st, so that the ranges' blocks share the GPU.
 template <class R>
 void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                   R* poly, int* flag, cudaStream_t st, const ForkJoin* fj) {
+  // the ghost slots beyond nc belong to the reconstruction: refresh them from the state first
+  if (m.ng > 0)
+    k_ghost_fill<R><<<blocks_for(m.ng, 128), 128, 0, st>>>(m.nc, m.ng, m.g_src, m.g_map,
+                                                            m.g_mapf, const_cast<R*>(QA));
   int used = 0;
   const bool fork = fj && fj->n > 0 && m.rr.n > 1;
   if (fork) cudaEventRecord(fj->fork, st);
@@ -992,20 +1064,12 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
                  double dt, R* fface, int* flag, cudaStream_t st) {
-  FluxParams<R> fp;
-  fp.gamma = p.gamma;
-  fp.K = p.K;
-  fp.mu = p.mu;
-  fp.tau_eps = p.tau_eps;
-  fp.tau_C = p.tau_C;
-  fp.full = p.flux_mode;
-  fp.tau_model = p.tau_model;
-  fp.pr_fix = p.pr_fix;
+  const FluxParams<R> fp = flux_params(p);
   const unsigned nb = blocks_for(4 * m.nf, 128);
   auto kern = fp.full ? (fp.tau_model == 0 ? k_flux<R, true, true> : k_flux<R, true, false>)
                       : (fp.tau_model == 0 ? k_flux<R, false, true> : k_flux<R, false, false>);
-  kern<<<nb, 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly, fp, (R)dt, fface,
-                           flag);
+  kern<<<nb, 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly, fp,
+                           wall_table<R>(m), (R)dt, fface, flag);
 }
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,
@@ -1042,26 +1106,27 @@ void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage,
 }
 template <class R>
 void launch_jacobi_init(const DevMesh& m, const R* fface, const R* fn, const double* vol,
-                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0, double gamma,
-                        cudaStream_t st) {
+                        double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0,
+                        const KParams<R>& kp, cudaStream_t st) {
   k_jacobi_init<R><<<blocks_for(m.nc, 256), 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner,
                                                           m.f_nb, m.f_wall, fface, fn, vol, dt,
-                                                          QA, (R)(gamma - 1.0), Rv, D, hrs, dQ0);
+                                                          QA, flux_params(kp), wall_table<R>(m),
+                                                          Rv, D, hrs, dQ0);
 }
 template <class R>
 void launch_jacobi_sweep(const DevMesh& m, const R* fn, const R* QA, const R* Rv, const R* D,
-                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout, double gamma,
-                         int* flag, cudaStream_t st) {
+                         const R* hrs, const R* dQin, R* dQout, int last, R* QAout,
+                         const KParams<R>& kp, int* flag, cudaStream_t st) {
   const unsigned nb = blocks_for(m.nc, 256);
-  const R gm1 = (R)(gamma - 1.0);
+  const FluxParams<R> fp = flux_params(kp);
   if (last)
     k_jacobi_sweep<R, true><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner, m.f_nb,
                                                 m.f_wall, fn, QA, Rv, D, hrs, dQin, dQout, QAout,
-                                                gm1, flag);
+                                                fp, wall_table<R>(m), flag);
   else
     k_jacobi_sweep<R, false><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, m.f_owner, m.f_nb,
                                                  m.f_wall, fn, QA, Rv, D, hrs, dQin, dQout, QAout,
-                                                 gm1, flag);
+                                                 fp, wall_table<R>(m), flag);
 }
 template <class R>
 void launch_unpack(int64_t nc, const R* QA, double* Q, cudaStream_t st) {
@@ -1083,9 +1148,11 @@ int dt_blocks(int64_t nc) {
   const int64_t b = (nc + kDtThreads - 1) / kDtThreads;
   return (int)(b < kDtMaxBlocks ? b : kDtMaxBlocks);
 }
-void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, double mu,
-               double* partial, int nblocks, double* out, cudaStream_t st) {
-  k_dt_partial<<<nblocks, kDtThreads, 0, st>>>(nc, Q, hdt, gamma, mu, partial);
+void launch_dt(int64_t nc, const double* Q, const double* hdt, double gamma, double mu, int power,
+               double T_ref, double mu_pow, double* partial, int nblocks, double* out,
+               cudaStream_t st) {
+  k_dt_partial<<<nblocks, kDtThreads, 0, st>>>(nc, Q, hdt, gamma, mu, power, T_ref, mu_pow,
+                                               partial);
   k_dt_final<<<1, 256, 0, st>>>(partial, nblocks, out);
 }
 
@@ -1112,17 +1179,17 @@ template void launch_stage<float>(const DevMesh&, const GeoR<float>&, const floa
 template void launch_unpack<double>(int64_t, const double*, double*, cudaStream_t);
 template void launch_jacobi_init<double>(const DevMesh&, const double*, const double*,
                                          const double*, double, const double*, double*, double*,
-                                         double*, double*, double, cudaStream_t);
+                                         double*, double*, const KParams<double>&, cudaStream_t);
 template void launch_jacobi_init<float>(const DevMesh&, const float*, const float*, const double*,
                                         double, const float*, float*, float*, float*, float*,
-                                        double, cudaStream_t);
+                                        const KParams<float>&, cudaStream_t);
 template void launch_jacobi_sweep<double>(const DevMesh&, const double*, const double*,
                                           const double*, const double*, const double*,
-                                          const double*, double*, int, double*, double, int*,
-                                          cudaStream_t);
+                                          const double*, double*, int, double*,
+                                          const KParams<double>&, int*, cudaStream_t);
 template void launch_jacobi_sweep<float>(const DevMesh&, const float*, const float*, const float*,
                                          const float*, const float*, const float*, float*, int,
-                                         float*, double, int*, cudaStream_t);
+                                         float*, const KParams<float>&, int*, cudaStream_t);
 template void launch_unpack<float>(int64_t, const float*, double*, cudaStream_t);
 
 }  // namespace gks

@@ -18,11 +18,22 @@ constexpr int kMaxStencil = 64;  // largest big stencil accepted
 constexpr int kMaxSub = 8;       // largest number of sub-stencils (hexahedra, pyramids)
 constexpr int kTile = 32;        // cells per tile of the interleaved stencil layouts
 
-// Affine per-axis map x' = s x + t between cell frames (periodic shift or mirror image).
+// Affine per-axis map x' = s x + t between cell frames (periodic shift or mirror image), with
+// the wall planes (axis + 3 side) the image was reflected across, in the order they apply, and
+// the momentum components that end up negated (vflip bit j). A stencil member crosses at most
+// two walls (a face of the cell and a face of a neighbour).
 struct Xf {
   int8_t s[3] = {1, 1, 1};
   double t[3] = {0, 0, 0};
+  uint8_t vflip = 0;
+  int8_t nw = 0;
+  int8_t w[2] = {-1, -1};
 };
+// Wall code of a face: -1 interior; axis + 3 side for a slip wall, 6 + axis + 3 side for a
+// no-slip wall.
+inline int wall_axis(int code) { return code % 3; }
+inline int wall_plane(int code) { return code % 6; }
+inline bool wall_noslip(int code) { return code >= 6; }
 
 // Host-side mesh after topology, stencil and ordering work. Cells and faces are in the
 // internal (Morton) order; perm maps internal cell -> caller cell.
@@ -35,7 +46,7 @@ struct HostMesh {
   std::vector<double> cell_x;          // [n][8][3] slot coordinates (internal order)
   // faces
   std::vector<int32_t> f_owner, f_nb;  // internal cell ids; nb = -1 on a reflecting wall
-  std::vector<int8_t> f_wall;          // wall axis or -1
+  std::vector<int8_t> f_wall;          // wall code (see wall_plane) or -1
   std::vector<double> f_vert;          // [nf][4][3] oriented vertices in the owner frame
   std::vector<double> f_shift;         // [nf][3] neighbour frame -> owner frame translation
   // cell -> face incidence, fixed local-face order: (face << 1) | (1 if the cell is the nb side)
@@ -43,6 +54,7 @@ struct HostMesh {
   // big stencil (without the cell itself) and sub-stencil membership
   std::vector<int32_t> st_ptr, st_idx;  // st_idx: cell | flip mask << kFlipShift
   std::vector<double> st_xf;            // [n_st][6]: s[3], t[3] of the member transform
+  std::vector<uint8_t> st_walls;        // wall planes crossed: (w0 + 1) | (w1 + 1) << 3, 0 none
   std::vector<uint8_t> st_sub;          // bit m set if the member is in sub-stencil m
   std::vector<int8_t> n_sub;            // M per cell
   std::vector<int32_t> sb_ptr;          // offset of each cell's (member, sub-stencil) pairs

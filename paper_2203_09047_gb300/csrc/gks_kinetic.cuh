@@ -18,6 +18,8 @@ GKS_HD double k_sqrt(double x) { return sqrt(x); }
 GKS_HD float k_sqrt(float x) { return sqrtf(x); }
 GKS_HD double k_abs(double x) { return fabs(x); }
 GKS_HD float k_abs(float x) { return fabsf(x); }
+GKS_HD double k_pow(double x, double y) { return pow(x, y); }
+GKS_HD float k_pow(float x, float y) { return powf(x, y); }
 
 // Moments <u^k>, <v^l>, <w^m>, <xi^(2x)> of a unit-density Maxwellian (u possibly over a
 // half line).
@@ -402,7 +404,132 @@ struct FluxParams {
   R gamma, K, mu, tau_eps, tau_C;
   int full, tau_model;
   R pr_fix = R(0);  // 1/Pr - 1 (heat-flux correction of the smooth flux; 0 for the BGK value)
+  R T_ref = R(1), mu_pow = R(0.7);  // power law mu (T / T_ref)^mu_pow (collision time 3)
 };
+
+// One no-slip wall plane: velocity and temperature (<= 0: adiabatic). The kernels read it from a
+// [6][4] device table (plane axis + 3 side) only at wall faces, so that the parameter block
+// holds no array indexed at run time.
+template <class R>
+struct WallData {
+  R uw[3] = {R(0), R(0), R(0)};
+  R Tw = R(0);
+};
+template <class R>
+GKS_HD WallData<R> wall_data(const R* table, int code) {
+  WallData<R> d;
+  if (code >= 6) {
+    const R* t = table + 4 * (code - 6);
+    d.uw[0] = t[0];
+    d.uw[1] = t[1];
+    d.uw[2] = t[2];
+    d.Tw = t[3];
+  }
+  return d;
+}
+
+// Flux parameters from the solver's kernel parameters (any struct with the same field names).
+template <class R, template <class> class KP>
+inline FluxParams<R> flux_params(const KP<R>& p) {
+  FluxParams<R> fp;
+  fp.gamma = p.gamma;
+  fp.K = p.K;
+  fp.mu = p.mu;
+  fp.tau_eps = p.tau_eps;
+  fp.tau_C = p.tau_C;
+  fp.full = p.flux_mode;
+  fp.tau_model = p.tau_model;
+  fp.pr_fix = p.pr_fix;
+  fp.T_ref = p.T_ref;
+  fp.mu_pow = p.mu_pow;
+  return fp;
+}
+
+// Collision time of the interface (Section 5): zero; inviscid (eps + C dp) dt; viscous
+// mu / p0 + C dp dt, with mu constant or the power law of Section 5.4 at T0 = p0 / rho0.
+template <class R>
+GKS_HD R collision_time(const FluxParams<R>& P, R p0, R ir0, R dp, R dt) {
+  if (P.tau_model == 1) return (P.tau_eps + P.tau_C * dp) * dt;
+  if (P.tau_model == 2) return P.mu / p0 + P.tau_C * dp * dt;
+  if (P.tau_model == 3) return P.mu * k_pow(p0 * ir0 / P.T_ref, P.mu_pow) / p0 + P.tau_C * dp * dt;
+  return R(0);
+}
+
+// Ghost value and gradient at a Gauss point of wall `code` (global frame; code as in
+// gks_internal.h: axis + 3 side, + 6 for a no-slip wall). Geometry is mirrored (d/dx_axis
+// changes sign); the flow variables: slip, the normal momentum negated; no-slip with (U_w, T_w),
+// rho_g = rho, m_g = 2 U_w rho - m and E_g = E + 2 |U_w|^2 rho - 2 U_w . m (adiabatic, p_g = p)
+// or E_g = 2 rho T_w / (gamma-1) - E + |m|^2/rho + 2 |U_w|^2 rho - 2 U_w . m (isothermal,
+// T_g = 2 T_w - T); the gradient is mapped by the Jacobian of that map.
+template <class R>
+GKS_HD void wall_ghost(const FluxParams<R>& P, int code, const WallData<R>& wd, const R v[5],
+                       const R g[5][3], R vg[5], R gg[5][3]) {
+  const int ax = code % 3;
+  if (code < 6) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const R sv = (r == 1 + ax) ? R(-1) : R(1);
+      vg[r] = sv * v[r];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) gg[r][b] = (b == ax ? -sv : sv) * g[r][b];
+    }
+    return;
+  }
+  const R u0 = wd.uw[0], u1 = wd.uw[1], u2 = wd.uw[2], Tw = wd.Tw;
+  const R uw2 = u0 * u0 + u1 * u1 + u2 * u2;
+  const R uw[3] = {u0, u1, u2};
+  // row 4 of the Jacobian: dE_g = j0 drho + jm . dm + j4 dE
+  R j0, jm[3], j4;
+  const R rho = v[0];
+  const R um = u0 * v[1] + u1 * v[2] + u2 * v[3];
+  if (Tw > R(0)) {
+    const R ir = R(1) / rho;
+    const R U[3] = {v[1] * ir, v[2] * ir, v[3] * ir};
+    const R U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+    const R cT = R(2) * Tw / (P.gamma - R(1));
+    vg[4] = cT * rho - v[4] + U2 * rho + R(2) * uw2 * rho - R(2) * um;
+    j0 = cT - U2 + R(2) * uw2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) jm[a] = R(2) * (U[a] - uw[a]);
+    j4 = R(-1);
+  } else {
+    vg[4] = v[4] + R(2) * uw2 * rho - R(2) * um;
+    j0 = R(2) * uw2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) jm[a] = R(-2) * uw[a];
+    j4 = R(1);
+  }
+  vg[0] = rho;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) vg[1 + a] = R(2) * uw[a] * rho - v[1 + a];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const R sb = b == ax ? R(-1) : R(1);
+    gg[0][b] = sb * g[0][b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gg[1 + a][b] = sb * (R(2) * uw[a] * g[0][b] - g[1 + a][b]);
+    gg[4][b] = sb * (j0 * g[0][b] + jm[0] * g[1][b] + jm[1] * g[2][b] + jm[2] * g[3][b] +
+                     j4 * g[4][b]);
+  }
+}
+
+// The wall flux (after the Gauss-point sum): no mass; a slip wall passes normal momentum only;
+// an adiabatic no-slip wall conducts no heat, so its energy flux is U_w . (momentum flux).
+template <class R>
+GKS_HD void wall_flux_fix(int code, const WallData<R>& wd, R acc[10]) {
+  acc[0] = acc[5] = R(0);
+  const int ax = code % 3;
+  if (code < 6) {
+#pragma unroll
+    for (int v = 1; v < 5; ++v)
+      if (v != 1 + ax) acc[v] = acc[5 + v] = R(0);
+    return;
+  }
+  if (wd.Tw <= R(0)) {
+    acc[4] = wd.uw[0] * acc[1] + wd.uw[1] * acc[2] + wd.uw[2] * acc[3];
+    acc[9] = wd.uw[0] * acc[6] + wd.uw[1] * acc[7] + wd.uw[2] * acc[8];
+  }
+}
 
 // Time integrals over [0, d] of the six coefficients of Eq. flux-1.
 template <class R>
@@ -463,10 +590,8 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
   for (int q = 0; q < 5; ++q) dWt[q] = -(dWt[q] + t[q]);
   euler_flux_x(w0, q0[4], E0);
   euler_jvp(w0, ir0, gm1, Ep0, 0, dWt, E2);
-  R tau = R(0);
   const R dp = k_abs((wl.p - wr.p) / (wl.p + wr.p));
-  if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
-  if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
+  const R tau = collision_time(P, w0.p, ir0, dp, dt);
   if (P.tau_model != 0) {
     // E1 = rho0 <u (ab . c) psi>_0 = sum_d D T_d(W0)[dW_d]
     second_moment_jvp(w0, ir0, gm1, P.K, 0, dW[0], E1);

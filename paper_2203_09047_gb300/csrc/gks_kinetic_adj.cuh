@@ -304,11 +304,9 @@ GKS_HD bool gks_gp_flux_vjp(const FluxParams<R>& P, const R ql[5], const R dql[3
   Gadotu(M0, ab, 0, bA);
   for (int q = 0; q < 5; ++q) bA[q] = -bA[q];
   slope_solve(w0.U, w0.V, w0.W, w0.lam, P.K, bA, Ab);
-  R tau = R(0);
   const R xdp = (wl.p - wr.p) / (wl.p + wr.p);
   const R dp = k_abs(xdp);
-  if (P.tau_model == 1) tau = (P.tau_eps + P.tau_C * dp) * dt;
-  if (P.tau_model == 2) tau = P.mu / w0.p + P.tau_C * dp * dt;
+  const R tau = collision_time(P, w0.p, R(1) / w0.rho, dp, dt);
   R e0[5], e1[5], e2[5];
   G(M0, 1, 0, 0, 0, e0);
   Ga(M0, Ab, 1, 0, 0, e2);
@@ -445,6 +443,13 @@ GKS_HD bool gks_gp_flux_vjp(const FluxParams<R>& P, const R ql[5], const R dql[3
   if (P.tau_model != 0) {
     R gdp = gtau * P.tau_C * dt;
     if (P.tau_model == 2) gw0.p += -gtau * P.mu / (w0.p * w0.p);
+    if (P.tau_model == 3) {
+      // tau_mu = mu (T0/T_ref)^s / p0, T0 = p0/rho0: d/dp0 = (s - 1) tau_mu / p0,
+      // d/drho0 = -s tau_mu / rho0
+      const R tmu = P.mu * k_pow(w0.p / (w0.rho * P.T_ref), P.mu_pow) / w0.p;
+      gw0.p += gtau * (P.mu_pow - R(1)) * tmu / w0.p;
+      gw0.rho += -gtau * P.mu_pow * tmu / w0.rho;
+    }
     const R gx = xdp < R(0) ? -gdp : gdp;
     const R s = wl.p + wr.p;
     gwl.p += gx * R(2) * wr.p / (s * s);
@@ -505,6 +510,97 @@ GKS_HD bool gks_gp_flux_vjp(const FluxParams<R>& P, const R ql[5], const R dql[3
   to_prim_adj(ql, P.gamma, wl, gwl, gql);
   to_prim_adj(qr, P.gamma, wr, gwr, gqr);
   return true;
+}
+
+// Reverse of wall_flux_fix: the cotangent of the treated face flux -> that of the summed one.
+template <class R>
+GKS_HD void wall_flux_fix_adj(int code, const WallData<R>& wd, R gacc[10]) {
+  gacc[0] = gacc[5] = R(0);
+  const int ax = code % 3;
+  if (code < 6) {
+#pragma unroll
+    for (int v = 1; v < 5; ++v)
+      if (v != 1 + ax) gacc[v] = gacc[5 + v] = R(0);
+    return;
+  }
+  if (wd.Tw <= R(0)) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      gacc[1 + a] += wd.uw[a] * gacc[4];
+      gacc[6 + a] += wd.uw[a] * gacc[9];
+    }
+    gacc[4] = gacc[9] = R(0);
+  }
+}
+
+// Reverse of wall_ghost: the cotangents (gvg, ggg) of the ghost value and gradient are added to
+// those (gv, gg) of the owner's. The slip and adiabatic maps are linear (the transposed Jacobian
+// and mirror); the isothermal map's energy row depends on U = m / rho also through the
+// gradient's Jacobian, which adds the second-order term.
+template <class R>
+GKS_HD void wall_ghost_vjp(const FluxParams<R>& P, int code, const WallData<R>& wd, const R v[5],
+                           const R g[5][3], const R gvg[5], const R ggg[5][3], R gv[5],
+                           R gg[5][3]) {
+  const int ax = code % 3;
+  if (code < 6) {
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const R sv = (r == 1 + ax) ? R(-1) : R(1);
+      gv[r] += sv * gvg[r];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) gg[r][b] += (b == ax ? -sv : sv) * ggg[r][b];
+    }
+    return;
+  }
+  const R uw[3] = {wd.uw[0], wd.uw[1], wd.uw[2]};
+  const R uw2 = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+  const bool iso = wd.Tw > R(0);
+  R j0, jm[3], j4, U[3] = {R(0), R(0), R(0)}, U2 = R(0), ir = R(0);
+  if (iso) {
+    ir = R(1) / v[0];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) U[a] = v[1 + a] * ir;
+    U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+    j0 = R(2) * wd.Tw / (P.gamma - R(1)) - U2 + R(2) * uw2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) jm[a] = R(2) * (U[a] - uw[a]);
+    j4 = R(-1);
+  } else {
+    j0 = R(2) * uw2;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) jm[a] = R(-2) * uw[a];
+    j4 = R(1);
+  }
+  // value: the Jacobian rows (1, 0..), (2 uw_a, -e_a, 0), (j0, jm, j4)
+  gv[0] += gvg[0] + R(2) * (uw[0] * gvg[1] + uw[1] * gvg[2] + uw[2] * gvg[3]) + j0 * gvg[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gv[1 + a] += -gvg[1 + a] + jm[a] * gvg[4];
+  gv[4] += j4 * gvg[4];
+  // gradient: the same Jacobian after the mirror sign of each direction
+  R D0 = R(0), Dm[3] = {R(0), R(0), R(0)};
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const R sb = b == ax ? R(-1) : R(1);
+    const R z0 = sb * ggg[0][b], z4 = sb * ggg[4][b];
+    R zm[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) zm[a] = sb * ggg[1 + a][b];
+    gg[0][b] += z0 + R(2) * (uw[0] * zm[0] + uw[1] * zm[1] + uw[2] * zm[2]) + j0 * z4;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gg[1 + a][b] += -zm[a] + jm[a] * z4;
+    gg[4][b] += j4 * z4;
+    D0 += z4 * g[0][b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Dm[a] += z4 * g[1 + a][b];
+  }
+  if (iso) {
+    // d j0 / d rho = 2 U2 / rho, d j0 / d m_a = -2 U_a / rho; d jm_a / d rho = -2 U_a / rho,
+    // d jm_a / d m_c = 2 delta_ac / rho
+    R UDm = U[0] * Dm[0] + U[1] * Dm[1] + U[2] * Dm[2];
+    gv[0] += R(2) * ir * (U2 * D0 - UDm);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) gv[1 + a] += R(2) * ir * (Dm[a] - U[a] * D0);
+  }
 }
 
 // Vector-Jacobian product of gp_flux_global: gacc[10] -> cotangents of vl, gl, vr, gr

@@ -74,6 +74,15 @@ Xf xf_compose(const Xf& a, const Xf& b) {  // a(b(x))
     c.s[k] = (int8_t)(a.s[k] * b.s[k]);
     c.t[k] = a.s[k] * b.t[k] + a.t[k];
   }
+  c.vflip = a.vflip ^ b.vflip;
+  for (int k = 0; k < b.nw; ++k) c.w[c.nw++] = b.w[k];
+  for (int k = 0; k < a.nw; ++k) {
+    if (c.nw == 2) {
+      c.nw = 3;  // more than two walls: rejected by the stencil builder
+      break;
+    }
+    c.w[c.nw++] = a.w[k];
+  }
   return c;
 }
 bool xf_equal(const Xf& a, const Xf& b, double tol) {
@@ -114,7 +123,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
   }
   double L[3], ext = 0;
   for (int a = 0; a < 3; ++a) {
-    if (bc[a] != GKS_BC_PERIODIC && bc[a] != GKS_BC_REFLECT) {
+    if (bc[a] != GKS_BC_PERIODIC && bc[a] != GKS_BC_REFLECT && bc[a] != GKS_BC_NOSLIP) {
       err = "unknown boundary condition";
       return GKS_E_INVAL;
     }
@@ -260,7 +269,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
       f.wall = -1;
       double plane = 0;
       for (int a = 0; a < 3 && f.wall < 0; ++a) {
-        if (bc[a] != GKS_BC_REFLECT) continue;
+        if (bc[a] != GKS_BC_REFLECT && bc[a] != GKS_BC_NOSLIP) continue;
         for (int side = 0; side < 2 && f.wall < 0; ++side) {
           const double pl = side ? hi[a] : lo[a];
           bool on = true;
@@ -269,7 +278,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
                           pl) > tol)
               on = false;
           if (on) {
-            f.wall = (int8_t)a;
+            f.wall = (int8_t)(a + 3 * side + (bc[a] == GKS_BC_NOSLIP ? 6 : 0));
             plane = pl;
           }
         }
@@ -279,7 +288,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
               ": unmatched face not on a reflecting boundary plane";
         return GKS_E_MESH;
       }
-      f.shift[f.wall] = 2.0 * plane;  // mirror: x' = -x + 2 plane on the wall axis
+      f.shift[wall_axis(f.wall)] = 2.0 * plane;  // mirror: x' = -x + 2 plane on the wall axis
     }
     // neighbour table entries
     if (f.nb >= 0) {
@@ -293,9 +302,13 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
       nbs[fptr[f.nb] + f.nf] = b;
     } else {
       Nb a;
+      const int ax = wall_axis(f.wall);
       a.cell = f.owner;
-      a.xf.s[f.wall] = -1;
-      a.xf.t[f.wall] = f.shift[f.wall];
+      a.xf.s[ax] = -1;
+      a.xf.t[ax] = f.shift[ax];
+      a.xf.vflip = (uint8_t)(wall_noslip(f.wall) ? 7 : 1 << ax);
+      a.xf.nw = 1;
+      a.xf.w[0] = (int8_t)wall_plane(f.wall);
       nbs[fptr[f.owner] + f.of] = a;
     }
     faces.push_back(f);
@@ -413,6 +426,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
   m.sb_ptr.assign(nc + 1, 0);
   m.sub_cnt.assign(nc, 0);
   m.st_idx.clear();
+  m.st_walls.clear();
   m.st_xf.clear();
   m.st_sub.clear();
   std::vector<Nb> list;
@@ -473,10 +487,13 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
     int pairs = 0;
     for (size_t k = 0; k < list.size(); ++k) {
       const Nb& e = list[k];
-      int flip = 0;
-      for (int a = 0; a < 3; ++a)
-        if (e.xf.s[a] < 0) flip |= 1 << a;
-      m.st_idx.push_back(inv[e.cell] | (flip << kFlipShift));
+      if (e.xf.nw > 2) {
+        err = "cell " + std::to_string(c) + ": a stencil member crosses more than two walls";
+        return GKS_E_MESH;
+      }
+      m.st_idx.push_back(inv[e.cell] | ((int32_t)e.xf.vflip << kFlipShift));
+      m.st_walls.push_back((uint8_t)((e.xf.nw > 0 ? e.xf.w[0] + 1 : 0) |
+                                     (e.xf.nw > 1 ? (e.xf.w[1] + 1) << 3 : 0)));
       for (int a = 0; a < 3; ++a) m.st_xf.push_back((double)e.xf.s[a]);
       for (int a = 0; a < 3; ++a) m.st_xf.push_back(e.xf.t[a]);
       m.st_sub.push_back(sub[k]);

@@ -12,7 +12,7 @@ namespace opc {
 
 struct Counter {
   int64_t flops = 0;    // +, -, *, / (an FMA counts as two)
-  int64_t special = 0;  // exp, erfc, sqrt
+  int64_t special = 0;  // exp, erfc, sqrt, pow
 };
 static Counter g_count;
 
@@ -39,6 +39,7 @@ inline bool operator!=(Op a, Op b) { return a.v != b.v; }
 inline Op k_exp(Op a) { ++g_count.special; return Op(std::exp(a.v)); }
 inline Op k_erfc(Op a) { ++g_count.special; return Op(std::erfc(a.v)); }
 inline Op k_sqrt(Op a) { ++g_count.special; return Op(std::sqrt(a.v)); }
+inline Op k_pow(Op a, Op b) { ++g_count.special; return Op(std::pow(a.v, b.v)); }
 inline Op k_abs(Op a) { return Op(std::fabs(a.v)); }
 
 struct ArrCoef {
