@@ -35,6 +35,11 @@
 //    (adiabatic) or T_g = 2 T_w - p/rho (isothermal), its gradient the mirrored gradient mapped
 //    by the Jacobian of that map; the wall flux has no mass component and, at an adiabatic wall,
 //    the energy component U_w . (momentum flux);
+//  * far field (Section 5.4, Riemann invariants): the ghost, in the stencils and at the Gauss
+//    points, is the characteristic boundary state of the source or owner state and the far
+//    field (R+ from inside, R- from the far field, entropy and tangential velocity from the
+//    upwind side; supersonic in- and outflow take one side whole), with no gradient at the
+//    Gauss points; its face flux is the plain GKS flux;
 //  * power-law viscosity (Section 5.4): tau = mu (T0/T_ref)^mu_pow / p0 + C dp dt with
 //    T0 = p0 / rho0 of the interface equilibrium;
 //  * implicit step (Section 4): the system is written with |Omega_i| (the printed Eq. jacobi
@@ -325,6 +330,7 @@ struct Params {
   int weno_linear;  // 1: use the linear weights (omega-bar = gamma), i.e. plain P0
   double T_ref, mu_pow;   // mu(T) = mu (T / T_ref)^mu_pow, T = p / rho (Section 5.4)
   double uw[6][3], Tw[6];  // per wall plane (axis + 3 side): velocity, temperature (<= 0: adiabatic)
+  double finf[5];          // far-field state: rho, U, V, W, p
 };
 Params read_params(const double* p) {
   Params q;
@@ -345,6 +351,7 @@ Params read_params(const double* p) {
     for (int a = 0; a < 3; ++a) q.uw[w][a] = p[13 + 4 * w + a];
     q.Tw[w] = p[13 + 4 * w + 3];
   }
+  for (int v = 0; v < 5; ++v) q.finf[v] = p[37 + v];
   return q;
 }
 
@@ -358,7 +365,7 @@ struct Face {
   int owner = -1, owner_face = -1, nb = -1, nb_face = -1;
   Xform nb_to_owner;  // neighbour frame -> owner frame (for a wall: the mirror image)
   int wall_axis = -1;
-  int wall_kind = 0;   // 1 slip, 2 no-slip (the box condition of its axis)
+  int wall_kind = 0;   // 1 slip, 2 no-slip, 3 far field (the box condition of its axis)
   int wall_plane = -1;  // axis + 3 side (side 1: the upper plane)
   double xg[4][3], n[4][3], w[4];  // Gauss points (owner frame), unit normals, area weights
   double area = 0.0;
@@ -573,7 +580,7 @@ int build_mesh(Mesh& m, bool lazy) {
       int axis = -1;
       double plane = 0;
       for (int a = 0; a < 3 && axis < 0; ++a) {
-        if (m.bc[a] != 1 && m.bc[a] != 2) continue;
+        if (m.bc[a] != 1 && m.bc[a] != 2 && m.bc[a] != 3) continue;
         for (double pl : {m.lo[a], m.hi[a]}) {
           bool on = true;
           for (int v : vo)
@@ -595,7 +602,7 @@ int build_mesh(Mesh& m, bool lazy) {
       f.wall_plane = axis + (std::fabs(plane - m.hi[axis]) <= tol ? 3 : 0);
       f.nb_to_owner.s[axis] = -1.0;
       f.nb_to_owner.t[axis] = 2.0 * plane;
-      f.nb_to_owner.vflip = f.wall_kind == 1 ? 1 << axis : 7;
+      f.nb_to_owner.vflip = f.wall_kind == 1 ? 1 << axis : f.wall_kind == 2 ? 7 : 0;
       f.nb_to_owner.nw = 1;
       f.nb_to_owner.walls[0] = f.wall_plane;
     }
@@ -751,6 +758,14 @@ void transform_state(const Mesh& m, const Params& P, const Xform& X, const T* q,
     const int pl = X.walls[k], ax = pl % 3;
     if (m.bc[ax] == 1) {
       out[1 + ax] = -out[1 + ax];
+      continue;
+    }
+    if (m.bc[ax] == 3) {  // far field: the characteristic boundary state of the image's source
+      double n[3] = {0, 0, 0};
+      n[ax] = pl >= 3 ? 1.0 : -1.0;
+      T in[5];
+      for (int v = 0; v < 5; ++v) in[v] = out[v];
+      farfield_state(P, in, n, out);
       continue;
     }
     const double* uw = P.uw[pl];
@@ -1197,6 +1212,67 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
   return ST_OK;
 }
 
+// Far-field state at a boundary of outward unit normal n (Section 5.4: inlet and outlet by
+// Riemann invariants). From the interior state q and the far field, the invariants along n
+// R+ = u_n + 2c/(gamma-1) (carried out of the domain) and R- = u_n - 2c/(gamma-1) (carried in)
+// are taken from the interior and the far field; the boundary u_n and c are their mean and
+// (gamma-1)/4 of their difference; the entropy p/rho^gamma and the tangential velocity come from
+// the side the flow comes from. Supersonic inflow takes the far field, supersonic outflow the
+// interior. Returns the conserved boundary state.
+template <class T>
+void farfield_state(const Params& P, const T* q, const double n[3], T* out) {
+  const double g = P.gamma, gm1 = g - 1.0;
+  const T rho = q[0];
+  T U[3], un = T(0.0), ke = T(0.0);
+  for (int a = 0; a < 3; ++a) {
+    U[a] = q[1 + a] / rho;
+    un += U[a] * n[a];
+    ke += U[a] * U[a];
+  }
+  const T p = gm1 * (q[4] - 0.5 * rho * ke);
+  const T c = sqrt(g * p / rho);
+  const double rinf = P.finf[0], pinf = P.finf[4];
+  const double* Uinf = P.finf + 1;
+  double uninf = 0;
+  for (int a = 0; a < 3; ++a) uninf += Uinf[a] * n[a];
+  const double cinf = std::sqrt(g * pinf / rinf);
+  auto set_prim = [&](T r, const T* V, T pr) {
+    out[0] = r;
+    T k = T(0.0);
+    for (int a = 0; a < 3; ++a) {
+      out[1 + a] = r * V[a];
+      k += V[a] * V[a];
+    }
+    out[4] = pr / gm1 + 0.5 * r * k;
+  };
+  if (val(un) >= val(c)) {  // supersonic outflow: everything from the interior
+    for (int v = 0; v < 5; ++v) out[v] = q[v];
+    return;
+  }
+  if (val(un) <= -val(c)) {  // supersonic inflow: everything from the far field
+    T V[3] = {T(Uinf[0]), T(Uinf[1]), T(Uinf[2])};
+    set_prim(T(rinf), V, T(pinf));
+    return;
+  }
+  const T Rp = un + 2.0 * c / gm1;
+  const T Rm = uninf - 2.0 * cinf / gm1;
+  const T unb = 0.5 * (Rp + Rm);
+  const T cb = 0.25 * gm1 * (Rp - Rm);
+  T s, Vt[3];
+  if (val(unb) >= 0.0) {  // outflow: entropy and tangential velocity of the interior
+    s = p / pow(rho, g);
+    for (int a = 0; a < 3; ++a) Vt[a] = U[a] - un * n[a];
+  } else {
+    s = T(pinf / std::pow(rinf, g));
+    for (int a = 0; a < 3; ++a) Vt[a] = T(Uinf[a] - uninf * n[a]);
+  }
+  const T rb = pow(cb * cb / (g * s), 1.0 / gm1);
+  const T pb = rb * cb * cb / g;
+  T V[3];
+  for (int a = 0; a < 3; ++a) V[a] = Vt[a] + unb * n[a];
+  set_prim(rb, V, pb);
+}
+
 // Ghost state at a wall point (Section 2: the ghost's flow variables follow the boundary
 // condition; the paper names slip, no-slip adiabatic and no-slip isothermal walls in Section 5
 // and gives no formulas). From the owner's value v and gradient g at the point (global frame),
@@ -1211,6 +1287,14 @@ template <class T>
 void wall_ghost(const Params& P, int kind, int plane, const T* v, const T g[5][3], T* vg,
                 T gg[5][3]) {
   const int ax = plane % 3;
+  if (kind == 3) {  // far field: the characteristic boundary state, uniform (no gradient)
+    double n[3] = {0, 0, 0};
+    n[ax] = plane >= 3 ? 1.0 : -1.0;
+    farfield_state(P, v, n, vg);
+    for (int r = 0; r < 5; ++r)
+      for (int b = 0; b < 3; ++b) gg[r][b] = T(0.0);
+    return;
+  }
   T J[5][5];
   for (int r = 0; r < 5; ++r)
     for (int c = 0; c < 5; ++c) J[r][c] = T(r == c ? 1.0 : 0.0);
@@ -1311,7 +1395,7 @@ bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& r
         for (int v = 0; v < 5; ++v) acc[s][v] += fc.w[k] * g[v];
       }
     }
-    if (fc.nb < 0) {
+    if (fc.nb < 0 && fc.wall_kind != 3) {
       // walls are impermeable: no mass flux. A slip wall passes only normal momentum (its
       // exact flux by symmetry); an adiabatic no-slip wall conducts no heat, so its energy flux
       // is the work of the wall force, U_w . F_m; an isothermal wall keeps the GKS energy flux
@@ -1413,6 +1497,13 @@ int step_implicit(const Mesh& m, const Params& P, double* Q, double dt, int nste
       get(dX, i, dq);
       double zg[5][3] = {}, zgg[5][3];
       wall_ghost(P, fc.wall_kind, fc.wall_plane, q, zg, qp, zgg);
+      if (fc.wall_kind == 3) {  // far field: the change of the characteristic state
+        double q1[5], g1[5];
+        for (int v = 0; v < 5; ++v) q1[v] = q[v] + dq[v];
+        wall_ghost(P, fc.wall_kind, fc.wall_plane, q1, zg, g1, zgg);
+        for (int v = 0; v < 5; ++v) dqp[v] = g1[v] - qp[v];
+        return;
+      }
       // the slip and adiabatic maps are linear: dQ_p = G(dQ_i)
       wall_ghost(P, fc.wall_kind, fc.wall_plane, dq, zg, dqp, zgg);
       if (fc.wall_kind == 2 && P.Tw[fc.wall_plane] > 0.0) {

@@ -224,3 +224,76 @@ def test_linear_shear_over_a_stationary_wall_has_the_exact_viscous_residual(tau_
     assert sel.sum() > 100
     np.testing.assert_allclose(L[:4, sel], 0.0, atol=1e-12)
     np.testing.assert_allclose(L[4, sel], muT * a * a, rtol=1e-9 if jitter == 0 else 0.15)
+
+
+# ------------------------------------------------------------------ far field (Riemann invariants)
+def _prim(q, gamma=GAMMA):
+    rho = q[0]
+    U = q[1:4] / rho
+    p = (gamma - 1) * (q[4] - 0.5 * rho * U @ U)
+    return rho, U, p, np.sqrt(gamma * p / rho)
+
+
+def _cons(rho, U, p, gamma=GAMMA):
+    return np.array([rho, *(rho * U), p / (gamma - 1) + 0.5 * rho * U @ U])
+
+
+FINF = (1.0, 0.3, -0.1, 0.05, 1.0 / GAMMA)   # rho, U, V, W, p: Mach 0.33
+
+
+@pytest.mark.parametrize("plane", [0, 1, 3, 5])
+def test_farfield_state_keeps_the_invariants(plane):
+    """Subsonic boundaries: the ghost carries the interior's outgoing invariant
+    R+ = u_n + 2c/(gamma-1) and the far field's incoming R- = u_n - 2c/(gamma-1) (n outward), and
+    the entropy p/rho^gamma and tangential velocity of the side the flow comes from; supersonic
+    outflow keeps the interior, supersonic inflow takes the far field; the far-field state is a
+    fixed point; the ghost has no gradient."""
+    rng = np.random.default_rng(90 + plane)
+    ax = plane % 3
+    n = np.zeros(3)
+    n[ax] = 1.0 if plane >= 3 else -1.0
+    P = oracle.params_vec(farfield=FINF)
+    qinf = _cons(FINF[0], np.array(FINF[1:4]), FINF[4])
+    g0 = rng.normal(size=(5, 3))
+    qg, gg = oracle.wall_ghost(P, 3, plane, qinf, g0)
+    np.testing.assert_allclose(qg, qinf, rtol=1e-14, atol=1e-15)
+    assert not gg.any()
+    ri, Ui, pi_, ci = _prim(qinf)
+    k = 2 / (GAMMA - 1)
+    for _ in range(6):
+        rho = 0.8 + 0.4 * rng.random()
+        p = 0.5 + 0.5 * rng.random()
+        c = np.sqrt(GAMMA * p / rho)
+        U = rng.normal(size=3) * 0.3
+        un = rng.uniform(-0.9, 0.9) * c
+        U += (un - U @ n) * n
+        q = _cons(rho, U, p)
+        qg, _ = oracle.wall_ghost(P, 3, plane, q, g0)
+        rb, Ub, pb, cb = _prim(qg)
+        unb = Ub @ n
+        np.testing.assert_allclose(unb + k * cb, un + k * c, rtol=1e-13)
+        np.testing.assert_allclose(unb - k * cb, Ui @ n - k * ci, rtol=1e-13, atol=1e-14)
+        src_rho, src_U, src_p = (rho, U, p) if unb >= 0 else (ri, Ui, pi_)
+        np.testing.assert_allclose(pb / rb ** GAMMA, src_p / src_rho ** GAMMA, rtol=1e-12)
+        np.testing.assert_allclose(Ub - unb * n, src_U - (src_U @ n) * n, atol=1e-13)
+    for sign in (1.0, -1.0):   # supersonic out- and inflow
+        rho, p = 1.1, 0.6
+        U = rng.normal(size=3) * 0.2
+        U += (sign * 1.5 * np.sqrt(GAMMA * p / rho) - U @ n) * n
+        q = _cons(rho, U, p)
+        qg, _ = oracle.wall_ghost(P, 3, plane, q, g0)
+        np.testing.assert_allclose(qg, q if sign > 0 else qinf, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("bc,finf", [((3, 3, 3), FINF), ((3, 3, 3), (1.0, 1.6, 0.3, -0.2, 1.0 / GAMMA)),
+                                     ((3, 1, 0), (1.2, 0.4, 0.0, 0.1, 0.9))])
+def test_farfield_box_preserves_the_free_stream(bc, finf):
+    """A uniform flow equal to the far field (subsonic and supersonic through all six planes;
+    with a slip wall along it) is a steady state: every ghost equals the flow."""
+    m, om = _box(bc)
+    q = _cons(finf[0], np.array(finf[1:4]), finf[4])
+    Q = np.tile(q[:, None], (1, om.n_cells))
+    for mode, tau in ((0, 0), (1, 2)):
+        P = oracle.params_vec(flux_mode=mode, tau_model=tau, mu=1e-3, farfield=finf)
+        L, Lt = om.residual(P, Q, 0.005)
+        assert np.abs(L).max() < 1e-12 and np.abs(Lt).max() < 1e-9
