@@ -47,8 +47,9 @@ typedef struct gks_solver gks_solver; /* opaque: device geometry, buffers, state
 enum { GKS_TET = 4, GKS_PYR = 5, GKS_PRI = 6, GKS_HEX = 8 };
 /* Boundary condition per axis of the bounding box: periodic; slip (reflecting) walls; no-slip
  * walls (Section 5: adiabatic or isothermal, possibly moving; their velocity and temperature are
- * solver parameters, wall_u and wall_T below). */
-enum { GKS_BC_PERIODIC = 0, GKS_BC_REFLECT = 1, GKS_BC_NOSLIP = 2 };
+ * solver parameters, wall_u and wall_T below); far field by Riemann invariants (Section 5.4;
+ * the far-field state is the solver parameter farfield). */
+enum { GKS_BC_PERIODIC = 0, GKS_BC_REFLECT = 1, GKS_BC_NOSLIP = 2, GKS_BC_FARFIELD = 3 };
 /* Flux variants (Section 3.2): the smooth flux of Eq. flux-2 read as
  * g0 [1 - tau (a.u + A) + t A], or the full flux of Eq. flux-1. */
 enum { GKS_FLUX_SMOOTH = 0, GKS_FLUX_FULL = 1 };
@@ -86,11 +87,18 @@ typedef struct {
    * on periodic and slip planes. The VJP supports adiabatic walls only. */
   double wall_u[6][3];
   double wall_T[6];
+  /* Far-field planes: the state (rho, U, V, W, p) outside. The ghost at a far-field plane, in
+   * the stencils and at the Gauss points, is the characteristic boundary state: the outgoing
+   * invariant u_n + 2c/(gamma-1) from inside, the incoming u_n - 2c/(gamma-1) from this state,
+   * entropy and tangential velocity from the upwind side (supersonic inflow: this state,
+   * supersonic outflow: the inside state); it carries no gradient at the Gauss points. The VJP
+   * rejects meshes with far-field planes. Default (1, 0, 0, 0, 1/1.4). */
+  double farfield[5];
 } gks_params;
 
 /* Fill *p with the defaults above (gamma 1.4, Euler, smooth flux, zero collision time,
  * weno_gamma 0.0125, weno_eps 1e-8, weno_pow 1, FP64, T_ref 1, mu_pow 0.7, stationary
- * adiabatic walls). */
+ * adiabatic walls, far field at rest with rho 1 and p 1/1.4). */
 void gks_params_default(gks_params* p);
 
 /* Build the mesh topology on the host.

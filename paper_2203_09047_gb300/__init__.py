@@ -23,7 +23,7 @@ STATUS_NAMES = ["GKS_OK", "GKS_E_INVAL", "GKS_E_NOMEM", "GKS_E_CUDA", "GKS_E_MES
                 "GKS_E_SINGULAR", "GKS_E_NONPHYSICAL", "GKS_E_TIMEOUT"]
 GKS_FLUX_SMOOTH, GKS_FLUX_FULL = 0, 1
 GKS_TAU_ZERO, GKS_TAU_INVISCID, GKS_TAU_VISCOUS, GKS_TAU_POWER_LAW = 0, 1, 2, 3
-GKS_BC_PERIODIC, GKS_BC_REFLECT, GKS_BC_NOSLIP = 0, 1, 2
+GKS_BC_PERIODIC, GKS_BC_REFLECT, GKS_BC_NOSLIP, GKS_BC_FARFIELD = 0, 1, 2, 3
 GKS_PREC_FP64, GKS_PREC_MIXED = 0, 1
 
 
@@ -34,7 +34,8 @@ class gks_params(ctypes.Structure):
                 ("weno_gamma", ctypes.c_double), ("weno_eps", ctypes.c_double),
                 ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int),
                 ("T_ref", ctypes.c_double), ("mu_pow", ctypes.c_double),
-                ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6)]
+                ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6),
+                ("farfield", ctypes.c_double * 5)]
 
 
 class GksError(RuntimeError):
@@ -139,6 +140,10 @@ def gks_params_default(**overrides) -> gks_params:
             v = np.asarray(v, dtype=np.float64).reshape(6)
             for w in range(6):
                 p.wall_T[w] = float(v[w])
+        elif k == "farfield":
+            v = np.asarray(v, dtype=np.float64).reshape(5)
+            for j in range(5):
+                p.farfield[j] = float(v[j])
         else:
             setattr(p, k, v)
     return p

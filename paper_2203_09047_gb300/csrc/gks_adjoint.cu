@@ -24,12 +24,17 @@ struct PolyRef64 {
   __device__ __forceinline__ double operator()(int v, int j) const { return p[10 * v + j]; }
 };
 
+// kFull and kTau0 fix the flux form and a zero collision time at compile time (as in the forward
+// kernel), so that each instance holds only its own form's recomputed forward state.
+template <bool kFull, bool kTau0>
 __global__ void __launch_bounds__(128) k_vjp_flux(
     int64_t nf, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const double* __restrict__ fgp,
     const double* __restrict__ poly, const double* __restrict__ gL, const double* __restrict__ gLt,
     const double* __restrict__ vol, int64_t nc, FluxParams<double> P,
     const double* __restrict__ wall_tab, double dt, double* __restrict__ gpf, int* flag) {
+  P.full = kFull;
+  if (kTau0) P.tau_model = 0;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t f = gid >> 2;
   const bool active = f < nf;
@@ -359,9 +364,11 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
                 double dt, double* gpf, double* gpc, double* gdq, double* gq0, double* gQ,
                 const int32_t* rs_ptr, const int32_t* rs_pos, int* flag, cudaStream_t st) {
   const FluxParams<double> fp = flux_params(p);
-  k_vjp_flux<<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.f_owner, m.f_nb, m.f_wall, g.fgp,
-                                                          poly, gL, gLt, g64.vol, m.nc, fp,
-                                                          m.wall64, dt, gpf, flag);
+  auto kern = fp.full ? (fp.tau_model == 0 ? k_vjp_flux<true, true> : k_vjp_flux<true, false>)
+                      : (fp.tau_model == 0 ? k_vjp_flux<false, true> : k_vjp_flux<false, false>);
+  kern<<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly,
+                                                  gL, gLt, g64.vol, m.nc, fp, m.wall64, dt, gpf,
+                                                  flag);
   k_vjp_poly<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, gpf, gpc);
   k_vjp_recon<<<blocks_for(m.nc, 64), 64, 0, st>>>(m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
                                                      m.t_idx, m.st_ptr, m.n_sub, g.Ap, g.Bp, g.mom,

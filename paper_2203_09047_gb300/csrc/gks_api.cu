@@ -153,6 +153,7 @@ KParams<R> kparams(const gks_params& p) {
   k.weno_pow = p.weno_pow;
   k.T_ref = (R)p.T_ref;
   k.mu_pow = (R)p.mu_pow;
+  for (int v = 0; v < 5; ++v) k.finf[v] = (R)p.farfield[v];
   return k;
 }
 
@@ -318,13 +319,14 @@ bool wall_map_is_signs(const WallMap& M) {
 // the entry's cell field.
 bool build_wall_ghosts(const HostMesh& h, const gks_params& p, std::vector<int32_t>& tidx,
                        std::vector<int32_t>& gsrc, std::vector<double>& gmap,
-                       std::vector<float>& gmapf) {
+                       std::vector<float>& gmapf, std::vector<uint8_t>& gchain) {
   tidx = h.t_idx;
   gsrc.clear();
   gmap.clear();
   gmapf.clear();
+  gchain.clear();
   bool any = false;
-  for (int a = 0; a < 3; ++a) any = any || h.bc[a] == GKS_BC_NOSLIP;
+  for (int a = 0; a < 3; ++a) any = any || h.bc[a] == GKS_BC_NOSLIP || h.bc[a] == GKS_BC_FARFIELD;
   if (!any) return true;
   const int64_t nc = h.n_cells;
   std::map<int64_t, int32_t> slot_of;  // (src << 8 | plane code) -> slot
@@ -337,8 +339,13 @@ bool build_wall_ghosts(const HostMesh& h, const gks_params& p, std::vector<int32
         const int64_t e = h.st_ptr[c] + k;
         const uint8_t code = h.st_walls[e];
         if (!code) continue;
-        const WallMap M = wall_map_of(h, p, code);
-        if (wall_map_is_signs(M)) continue;
+        bool far = false;
+        for (int q = 0; q < 2; ++q) {
+          const int w = ((code >> (3 * q)) & 7) - 1;
+          far = far || (w >= 0 && h.bc[w % 3] == GKS_BC_FARFIELD);
+        }
+        const WallMap M = far ? WallMap() : wall_map_of(h, p, code);
+        if (!far && wall_map_is_signs(M)) continue;
         const int32_t src = h.st_idx[e] & kCellMask;
         const int64_t key = ((int64_t)src << 8) | code;
         auto it = slot_of.find(key);
@@ -347,6 +354,7 @@ bool build_wall_ghosts(const HostMesh& h, const gks_params& p, std::vector<int32
           g = (int32_t)gsrc.size();
           slot_of.emplace(key, g);
           gsrc.push_back(src);
+          gchain.push_back(far ? code : 0);
           const double v[10] = {M.s[0], M.s[1], M.s[2], M.a[0], M.a[1], M.a[2], M.b,
                                 M.c[0], M.c[1], M.c[2]};
           for (double x : v) {
@@ -385,6 +393,11 @@ bool valid_params(const gks_params* p, std::string& why) {
       why = "wall velocity and temperature must be finite";
       return false;
     }
+  if (!(p->farfield[0] > 0.0 && p->farfield[4] > 0.0 && std::isfinite(p->farfield[1]) &&
+        std::isfinite(p->farfield[2]) && std::isfinite(p->farfield[3]))) {
+    why = "the far-field state needs rho > 0, p > 0 and a finite velocity";
+    return false;
+  }
   if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
   if (!(p->weno_eps > 0.0)) { why = "weno_eps must be > 0"; return false; }
   if (p->weno_pow < 1 || p->weno_pow > 4) { why = "weno_pow must be 1..4"; return false; }
@@ -459,6 +472,9 @@ void gks_params_default(gks_params* p) {
     p->wall_u[w][0] = p->wall_u[w][1] = p->wall_u[w][2] = 0.0;
     p->wall_T[w] = 0.0;
   }
+  p->farfield[0] = 1.0;
+  p->farfield[1] = p->farfield[2] = p->farfield[3] = 0.0;
+  p->farfield[4] = 1.0 / 1.4;
 }
 
 gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
@@ -554,7 +570,8 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
     std::vector<int32_t> tidx, gsrc;
     std::vector<double> gmap;
     std::vector<float> gmapf;
-    if (!build_wall_ghosts(h, *p, tidx, gsrc, gmap, gmapf)) {
+    std::vector<uint8_t> gchain;
+    if (!build_wall_ghosts(h, *p, tidx, gsrc, gmap, gmapf, gchain)) {
       g_mesh_err = "too many wall ghost cells for the stencil entry format";
       gks_destroy(s);
       return GKS_E_MESH;
@@ -574,7 +591,9 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
       if ((e = supload(s, &m.g_src, gsrc)) != cudaSuccess) return bad("upload");
       if ((e = supload(s, &m.g_map, gmap)) != cudaSuccess) return bad("upload");
       if ((e = supload(s, &m.g_mapf, gmapf)) != cudaSuccess) return bad("upload");
+      if ((e = supload(s, &m.g_chain, gchain)) != cudaSuccess) return bad("upload");
     }
+    m.bcs = h.bc[0] | (h.bc[1] << 2) | (h.bc[2] << 4);
   }
   // tile ranges by the kind of each tile's first cell (at most one per kind: cells are ordered
   // by kind first); a new range is opened only while slots remain, else the last one grows
@@ -751,6 +770,9 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
                             const double* gLt, double* gQ) {
   if (!s || !Q || !gL || !gLt || !gQ || !(dt > 0)) return GKS_E_INVAL;
   if (s->prm.Pr != 1.0) return s->fail(GKS_E_INVAL, "the VJP supports Pr = 1 only");
+  for (int a = 0; a < 3; ++a)
+    if (((s->m.bcs >> (2 * a)) & 3) == GKS_BC_FARFIELD)
+      return s->fail(GKS_E_INVAL, "the VJP does not support far-field planes");
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e = cudaSuccess;
   if (!s->vjp_ready) {

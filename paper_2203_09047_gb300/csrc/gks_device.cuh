@@ -91,6 +91,11 @@ struct DevMesh {
   int32_t* g_src = nullptr;
   double* g_map = nullptr;
   float* g_mapf = nullptr;
+  // slots whose image crossed a far-field plane are not linear: g_chain holds their planes
+  // ((w0 + 1) | (w1 + 1) << 3, applied in order, 0 for a linear slot) and bcs the box condition
+  // of each axis (2 bits per axis)
+  uint8_t* g_chain = nullptr;
+  int bcs = 0;
   // no-slip wall planes (axis + 3 side): velocity and temperature, [6][4] in FP64 and FP32
   double* wall64 = nullptr;
   float* wall32 = nullptr;
@@ -132,6 +137,7 @@ struct KParams {
   R weno_gamma, weno_eps;
   int weno_pow;
   R T_ref, mu_pow;  // power-law viscosity (the wall planes live in DevMesh::wall64/wall32)
+  R finf[5];        // far-field state rho, U, V, W, p
 };
 
 // ---- precompute (gks_geom.cu) -------------------------------------------------------------

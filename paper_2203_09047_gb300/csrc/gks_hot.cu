@@ -730,6 +730,16 @@ __device__ __forceinline__ void wall_cell_ghost_inc(const FluxParams<R>& P, int 
                                                     const R d[5], R dg[5]) {
   const R zg[5][3] = {};
   R gg[5][3];
+  if (code >= 12) {  // far field: the change of the characteristic state
+    R q1[5], g0[5], g1[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q1[v] = q[v] + d[v];
+    wall_ghost(P, code, wd, q, zg, g0, gg);
+    wall_ghost(P, code, wd, q1, zg, g1, gg);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) dg[v] = g1[v] - g0[v];
+    return;
+  }
   if (code < 6 || wd.Tw <= R(0)) {
     wall_ghost(P, code, wd, d, zg, dg, gg);
     return;
@@ -988,16 +998,56 @@ void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p,
       m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag);
 }
 
-// Ghost slots of moving no-slip walls: QA[nc + g] = map g applied to QA[g_src[g]].
+// Ghost slots of moving no-slip walls and far-field planes: QA[nc + g] = the image's flow
+// variables from QA[g_src[g]]. Linear slots apply their composed map; the others apply the
+// maps of their planes in order (slip: normal momentum negated; no-slip: rho kept,
+// m -> 2 U_w rho - m, E -> E + 2 |U_w|^2 rho - 2 U_w . m; far field: the characteristic
+// state), in precision R.
 template <class R>
 __global__ void __launch_bounds__(128) k_ghost_fill(int64_t nc, int64_t ng,
                                                     const int32_t* __restrict__ src,
                                                     const double* __restrict__ map,
-                                                    const float* __restrict__ mapf, R* QA) {
+                                                    const float* __restrict__ mapf,
+                                                    const uint8_t* __restrict__ chain, int bcs,
+                                                    FluxParams<R> P, const R* __restrict__ wall_tab,
+                                                    R* QA) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= ng) return;
   Gq<R> g;
   g.load(QA, src[k]);
+  if (const int code = chain[k]) {
+    R q[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) q[v] = (R)g.value(v);
+    for (int s = 0; s < 2; ++s) {
+      const int w = ((code >> (3 * s)) & 7) - 1;
+      if (w < 0) break;
+      const int ax = w % 3, kind = (bcs >> (2 * ax)) & 3;
+      if (kind == 1) {
+        q[1 + ax] = -q[1 + ax];
+      } else if (kind == 2) {
+        const R* t = wall_tab + 4 * w;
+        const R um = t[0] * q[1] + t[1] * q[2] + t[2] * q[3];
+        q[4] = q[4] + R(2) * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]) * q[0] - R(2) * um;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[1 + a] = R(2) * t[a] * q[0] - q[1 + a];
+      } else {
+        R o[5];
+        farfield_state(P, ax, w >= 3 ? R(1) : R(-1), q, o);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) q[v] = o[v];
+      }
+    }
+    if constexpr (std::is_same<R, float>::value) {
+      ff o[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) o[v] = ff{q[v], 0.f};
+      Gq<float>::store_ff(QA, nc + k, o);
+    } else {
+      Gq<double>::store(QA, nc + k, q);
+    }
+    return;
+  }
   if constexpr (std::is_same<R, float>::value) {
     const float* c = mapf + 20 * k;
     auto co = [&](int j) { return ff{c[2 * j], c[2 * j + 1]}; };
@@ -1035,8 +1085,9 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
                   R* poly, int* flag, cudaStream_t st, const ForkJoin* fj) {
   // the ghost slots beyond nc belong to the reconstruction: refresh them from the state first
   if (m.ng > 0)
-    k_ghost_fill<R><<<blocks_for(m.ng, 128), 128, 0, st>>>(m.nc, m.ng, m.g_src, m.g_map,
-                                                            m.g_mapf, const_cast<R*>(QA));
+    k_ghost_fill<R><<<blocks_for(m.ng, 128), 128, 0, st>>>(
+        m.nc, m.ng, m.g_src, m.g_map, m.g_mapf, m.g_chain, m.bcs, flux_params(p),
+        wall_table<R>(m), const_cast<R*>(QA));
   int used = 0;
   const bool fork = fj && fj->n > 0 && m.rr.n > 1;
   if (fork) cudaEventRecord(fj->fork, st);

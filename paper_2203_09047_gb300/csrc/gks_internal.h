@@ -30,10 +30,11 @@ struct Xf {
   int8_t w[2] = {-1, -1};
 };
 // Wall code of a face: -1 interior; axis + 3 side for a slip wall, 6 + axis + 3 side for a
-// no-slip wall.
+// no-slip wall, 12 + axis + 3 side for a far-field plane.
 inline int wall_axis(int code) { return code % 3; }
 inline int wall_plane(int code) { return code % 6; }
-inline bool wall_noslip(int code) { return code >= 6; }
+inline bool wall_noslip(int code) { return code >= 6 && code < 12; }
+inline bool wall_farfield(int code) { return code >= 12; }
 
 // Host-side mesh after topology, stencil and ordering work. Cells and faces are in the
 // internal (Morton) order; perm maps internal cell -> caller cell.

@@ -405,6 +405,7 @@ struct FluxParams {
   int full, tau_model;
   R pr_fix = R(0);  // 1/Pr - 1 (heat-flux correction of the smooth flux; 0 for the BGK value)
   R T_ref = R(1), mu_pow = R(0.7);  // power law mu (T / T_ref)^mu_pow (collision time 3)
+  R finf[5] = {R(1), R(0), R(0), R(0), R(1.0 / 1.4)};  // far field: rho, U, V, W, p
 };
 
 // One no-slip wall plane: velocity and temperature (<= 0: adiabatic). The kernels read it from a
@@ -418,7 +419,7 @@ struct WallData {
 template <class R>
 GKS_HD WallData<R> wall_data(const R* table, int code) {
   WallData<R> d;
-  if (code >= 6) {
+  if (code >= 6 && code < 12) {
     const R* t = table + 4 * (code - 6);
     d.uw[0] = t[0];
     d.uw[1] = t[1];
@@ -442,6 +443,7 @@ inline FluxParams<R> flux_params(const KP<R>& p) {
   fp.pr_fix = p.pr_fix;
   fp.T_ref = p.T_ref;
   fp.mu_pow = p.mu_pow;
+  for (int v = 0; v < 5; ++v) fp.finf[v] = p.finf[v];
   return fp;
 }
 
@@ -455,6 +457,51 @@ GKS_HD R collision_time(const FluxParams<R>& P, R p0, R ir0, R dp, R dt) {
   return R(0);
 }
 
+// Far-field state at a plane of axis ax with outward normal sign sg (Section 5.4, Riemann
+// invariants): R+ = u_n + 2c/(gamma-1) from the inside state q, R- = u_n - 2c/(gamma-1) from
+// the far field; u_n and c of the boundary are their mean and (gamma-1)/4 of their difference;
+// entropy p/rho^gamma and tangential velocity from the upwind side; supersonic inflow takes the
+// far field, supersonic outflow q. Conserved variables in and out.
+template <class R>
+GKS_HD void farfield_state(const FluxParams<R>& P, int ax, R sg, const R q[5], R out[5]) {
+  const R g = P.gamma, gm1 = P.gamma - R(1);
+  const R ir = R(1) / q[0];
+  const R U[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const R p = gm1 * (q[4] - R(0.5) * (q[1] * U[0] + q[2] * U[1] + q[3] * U[2]));
+  const R c = k_sqrt(g * p * ir);
+  const R un = sg * U[ax];
+  const R rinf = P.finf[0], pinf = P.finf[4];
+  const R Uinf[3] = {P.finf[1], P.finf[2], P.finf[3]};
+  const R uninf = sg * Uinf[ax];
+  const R cinf = k_sqrt(g * pinf / rinf);
+  R rb, pb, Ub[3];
+  if (un >= c) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) out[v] = q[v];
+    return;
+  }
+  if (un <= -c) {
+    rb = rinf;
+    pb = pinf;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Ub[a] = Uinf[a];
+  } else {
+    const R Rp = un + R(2) * c / gm1, Rm = uninf - R(2) * cinf / gm1;
+    const R unb = R(0.5) * (Rp + Rm), cb = R(0.25) * gm1 * (Rp - Rm);
+    const bool out_flow = unb >= R(0);
+    const R s = out_flow ? p / k_pow(q[0], g) : pinf / k_pow(rinf, g);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Ub[a] = out_flow ? U[a] : Uinf[a];
+    Ub[ax] = sg * unb;  // tangential components kept, the normal one from the invariants
+    rb = k_pow(cb * cb / (g * s), R(1) / gm1);
+    pb = rb * cb * cb / g;
+  }
+  out[0] = rb;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[1 + a] = rb * Ub[a];
+  out[4] = pb / gm1 + R(0.5) * rb * (Ub[0] * Ub[0] + Ub[1] * Ub[1] + Ub[2] * Ub[2]);
+}
+
 // Ghost value and gradient at a Gauss point of wall `code` (global frame; code as in
 // gks_internal.h: axis + 3 side, + 6 for a no-slip wall). Geometry is mirrored (d/dx_axis
 // changes sign); the flow variables: slip, the normal momentum negated; no-slip with (U_w, T_w),
@@ -465,6 +512,14 @@ template <class R>
 GKS_HD void wall_ghost(const FluxParams<R>& P, int code, const WallData<R>& wd, const R v[5],
                        const R g[5][3], R vg[5], R gg[5][3]) {
   const int ax = code % 3;
+  if (code >= 12) {  // far field: the characteristic state, uniform
+    farfield_state(P, ax, (code % 6) >= 3 ? R(1) : R(-1), v, vg);
+#pragma unroll
+    for (int r = 0; r < 5; ++r)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) gg[r][b] = R(0);
+    return;
+  }
   if (code < 6) {
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
@@ -517,6 +572,7 @@ GKS_HD void wall_ghost(const FluxParams<R>& P, int code, const WallData<R>& wd, 
 // an adiabatic no-slip wall conducts no heat, so its energy flux is U_w . (momentum flux).
 template <class R>
 GKS_HD void wall_flux_fix(int code, const WallData<R>& wd, R acc[10]) {
+  if (code >= 12) return;  // a far-field plane passes the GKS flux of its ghost pair
   acc[0] = acc[5] = R(0);
   const int ax = code % 3;
   if (code < 6) {

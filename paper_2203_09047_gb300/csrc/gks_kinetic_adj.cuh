@@ -515,6 +515,7 @@ GKS_HD bool gks_gp_flux_vjp(const FluxParams<R>& P, const R ql[5], const R dql[3
 // Reverse of wall_flux_fix: the cotangent of the treated face flux -> that of the summed one.
 template <class R>
 GKS_HD void wall_flux_fix_adj(int code, const WallData<R>& wd, R gacc[10]) {
+  if (code >= 12) return;  // far field: the flux passes unchanged
   gacc[0] = gacc[5] = R(0);
   const int ax = code % 3;
   if (code < 6) {
@@ -542,6 +543,7 @@ GKS_HD void wall_ghost_vjp(const FluxParams<R>& P, int code, const WallData<R>& 
                            const R g[5][3], const R gvg[5], const R ggg[5][3], R gv[5],
                            R gg[5][3]) {
   const int ax = code % 3;
+  if (code >= 12) return;  // far-field planes: the VJP entry point rejects such meshes
   if (code < 6) {
 #pragma unroll
     for (int r = 0; r < 5; ++r) {

@@ -123,7 +123,8 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
   }
   double L[3], ext = 0;
   for (int a = 0; a < 3; ++a) {
-    if (bc[a] != GKS_BC_PERIODIC && bc[a] != GKS_BC_REFLECT && bc[a] != GKS_BC_NOSLIP) {
+    if (bc[a] != GKS_BC_PERIODIC && bc[a] != GKS_BC_REFLECT && bc[a] != GKS_BC_NOSLIP &&
+        bc[a] != GKS_BC_FARFIELD) {
       err = "unknown boundary condition";
       return GKS_E_INVAL;
     }
@@ -269,7 +270,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
       f.wall = -1;
       double plane = 0;
       for (int a = 0; a < 3 && f.wall < 0; ++a) {
-        if (bc[a] != GKS_BC_REFLECT && bc[a] != GKS_BC_NOSLIP) continue;
+        if (bc[a] == GKS_BC_PERIODIC) continue;
         for (int side = 0; side < 2 && f.wall < 0; ++side) {
           const double pl = side ? hi[a] : lo[a];
           bool on = true;
@@ -278,7 +279,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
                           pl) > tol)
               on = false;
           if (on) {
-            f.wall = (int8_t)(a + 3 * side + (bc[a] == GKS_BC_NOSLIP ? 6 : 0));
+            f.wall = (int8_t)(a + 3 * side + 6 * (bc[a] - GKS_BC_REFLECT));
             plane = pl;
           }
         }
@@ -306,7 +307,7 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
       a.cell = f.owner;
       a.xf.s[ax] = -1;
       a.xf.t[ax] = f.shift[ax];
-      a.xf.vflip = (uint8_t)(wall_noslip(f.wall) ? 7 : 1 << ax);
+      a.xf.vflip = (uint8_t)(wall_farfield(f.wall) ? 0 : wall_noslip(f.wall) ? 7 : 1 << ax);
       a.xf.nw = 1;
       a.xf.w[0] = (int8_t)wall_plane(f.wall);
       nbs[fptr[f.owner] + f.of] = a;

@@ -25,12 +25,14 @@ def lib():
     return gks.load_library()
 
 
-def _hp(mode, tau_model, mu=2e-3, Pr=1.0, T_ref=T_REF, mu_pow=0.7, wall_u=None, wall_T=None):
+def _hp(mode, tau_model, mu=2e-3, Pr=1.0, T_ref=T_REF, mu_pow=0.7, wall_u=None, wall_T=None,
+        farfield=(1.0, 0.0, 0.0, 0.0, 1.0 / 1.4)):
     """Parameter vector of the host entries: gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr,
-    T_ref, mu_pow, wall_u[6][3], wall_T[6]."""
+    T_ref, mu_pow, wall_u[6][3], wall_T[6], farfield[5]."""
     wu = np.zeros(18) if wall_u is None else np.asarray(wall_u, dtype=np.float64).ravel()
     wT = np.zeros(6) if wall_T is None else np.asarray(wall_T, dtype=np.float64).ravel()
-    return np.concatenate([[1.4, mu, 0.01, 1.0, mode, tau_model, Pr, T_ref, mu_pow], wu, wT])
+    return np.concatenate([[1.4, mu, 0.01, 1.0, mode, tau_model, Pr, T_ref, mu_pow], wu, wT,
+                           farfield])
 
 
 def _state(rng):
@@ -227,3 +229,28 @@ def test_wall_flux_fix(lib):
         elif Tw[pl] <= 0:
             exp[4], exp[9] = uw[pl] @ acc[1:4], uw[pl] @ acc[6:9]
         np.testing.assert_allclose(out, exp, rtol=1e-15, atol=1e-16)  # dot-product rounding
+
+
+@pytest.mark.parametrize("code", [12, 13, 15, 17])
+def test_farfield_ghost_matches_oracle(lib, code):
+    """Far-field planes (codes 12 + axis + 3 side): the characteristic state against the
+    oracle, subsonic in- and outflow and both supersonic limits."""
+    rng = np.random.default_rng(500 + code)
+    finf = (1.05, 0.25, -0.1, 0.08, 0.7)
+    P = _hp(0, 2, farfield=finf)
+    Po = oracle.params_vec(flux_mode=0, tau_model=2, mu=2e-3, farfield=finf)
+    ax = code % 3
+    sg = 1.0 if (code % 6) >= 3 else -1.0
+    for mach_n in (-1.6, -0.5, 0.3, 0.8, 1.4):
+        v = _state(rng)
+        rho, U = v[0], v[1:4] / v[0]
+        p = 0.4 * (v[4] - 0.5 * rho * U @ U)
+        U[ax] = sg * mach_n * np.sqrt(1.4 * p / rho)
+        v = np.array([rho, *(rho * U), p / 0.4 + 0.5 * rho * U @ U])
+        g = rng.normal(size=(5, 3))
+        vg, gg = np.zeros(5), np.zeros(15)
+        lib.gks_wall_ghost_host(_d(P), code, _d(v), _d(g), vg.ctypes.data_as(D),
+                                gg.ctypes.data_as(D), None, None, None, None)
+        vo, go = oracle.wall_ghost(Po, 3, code - 12, v, g)
+        np.testing.assert_allclose(vg, vo, rtol=1e-13, atol=1e-14)
+        assert not gg.any() and not go.any()

@@ -181,3 +181,63 @@ def test_closed_noslip_box_conserves_mass_and_energy():
         tot1 = (S.get_state() * vol).sum(dim=1)
         for v in (0, 4):
             assert abs(float(tot1[v] - tot0[v])) <= 1e-12 * abs(float(tot0[v]))
+
+
+# ------------------------------------------------------------------ far field (Riemann invariants)
+FINF = (1.0, 0.3, -0.1, 0.05, 1.0 / 1.4)
+
+
+def farfield_state(om, seed, finf=FINF):
+    r, U, p = finf[0], np.array(finf[1:4]), finf[4]
+    q = np.array([r, *(r * U), p / 0.4 + 0.5 * r * U @ U])
+    return I.perturbed_state(np.tile(q[:, None], (1, om.n_cells)), seed=seed, amp=0.03)
+
+
+@pytest.mark.parametrize("bc", [(3, 3, 3), (3, 1, 2)])
+def test_farfield_residual_matches_oracle(bc):
+    """Far-field planes (all six; or x far field with a slip y wall and a moving no-slip z wall):
+    ghost cells reached across far-field planes are refreshed from the characteristic map."""
+    m, om = mesh_pair(8, "hybrid8", bc)
+    uw = np.zeros((6, 3))
+    uw[5] = (0.1, -0.05, 0.0)
+    p = dict(flux_mode=1, tau_model=2, mu=2e-3)
+    Q = farfield_state(om, seed=60)
+    Lo, Lto = om.residual(oracle.params_vec(wall_u=uw, farfield=FINF, **p), Q, 0.004)
+    for prec, tol in ((gks.GKS_PREC_FP64, FP64_TOL), (gks.GKS_PREC_MIXED, MIXED_TOL_L)):
+        S = gks.Solver(m, precision=prec, wall_u=uw, farfield=FINF, **p)
+        L, Lt = S.residual(Q, 0.004)
+        assert rel(L.cpu(), Lo) < tol
+        if prec == gks.GKS_PREC_FP64:
+            assert rel(Lt.cpu(), Lto) < tol
+
+
+def test_farfield_steps_and_implicit_match_oracle():
+    m, om = mesh_pair(8, "hybrid8", (3, 3, 3))
+    p = dict(flux_mode=0, tau_model=2, mu=2e-3)
+    P = oracle.params_vec(farfield=FINF, **p)
+    Q = farfield_state(om, seed=61)
+    S = gks.Solver(m, farfield=FINF, **p)
+    S.set_state(Q)
+    dt = S.max_dt(0.4)
+    S.step(dt, 3)
+    assert rel(S.get_state().cpu(), om.step(P, Q, dt, 3)) < FP64_TOL
+    S.set_state(Q)
+    S.step_implicit(4 * dt, 2, 3)
+    assert rel(S.get_state().cpu(), om.step_implicit(P, Q, 4 * dt, 2, 3)) < FP64_TOL
+    with pytest.raises(gks.GksError):
+        gL, gLt, _ = I.normal_directions(Q.shape, 3, 62)
+        S.residual_vjp(Q, dt, gL, gLt)
+
+
+@pytest.mark.parametrize("finf", [FINF, (1.0, 1.6, 0.3, -0.2, 1.0 / 1.4)])
+def test_farfield_box_keeps_the_free_stream(finf):
+    m, om = mesh_pair(8, "hybrid8", (3, 3, 3))
+    r, U, p = finf[0], np.array(finf[1:4]), finf[4]
+    q = np.array([r, *(r * U), p / 0.4 + 0.5 * r * U @ U])
+    Q = np.tile(q[:, None], (1, om.n_cells))
+    for prec, tol in ((gks.GKS_PREC_FP64, 1e-13), (gks.GKS_PREC_MIXED, 1e-6)):
+        S = gks.Solver(m, precision=prec, flux_mode=1, tau_model=1, farfield=finf)
+        S.set_state(Q)
+        S.step(2e-3, 3)
+        err = np.abs(S.get_state().cpu().numpy() - Q).max()
+        assert err < tol * np.abs(Q).max(), err
