@@ -92,8 +92,9 @@ typedef struct {
    * invariant u_n + 2c/(gamma-1) from inside, the incoming u_n - 2c/(gamma-1) from this state,
    * entropy and tangential velocity from the upwind side (supersonic inflow: this state,
    * supersonic outflow: the inside state); it carries no gradient at the Gauss points. The VJP
-   * rejects meshes with far-field planes. Default (1, 0, 0, 0, 1/1.4). */
-  double farfield[5];
+   * rejects meshes with far-field planes. One state per plane (axis + 3 side), default
+   * (1, 0, 0, 0, 1/1.4). */
+  double farfield[6][5];
 } gks_params;
 
 /* Fill *p with the defaults above (gamma 1.4, Euler, smooth flux, zero collision time,

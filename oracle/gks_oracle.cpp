@@ -330,7 +330,7 @@ struct Params {
   int weno_linear;  // 1: use the linear weights (omega-bar = gamma), i.e. plain P0
   double T_ref, mu_pow;   // mu(T) = mu (T / T_ref)^mu_pow, T = p / rho (Section 5.4)
   double uw[6][3], Tw[6];  // per wall plane (axis + 3 side): velocity, temperature (<= 0: adiabatic)
-  double finf[5];          // far-field state: rho, U, V, W, p
+  double finf[6][5];       // far-field state per plane: rho, U, V, W, p
 };
 Params read_params(const double* p) {
   Params q;
@@ -351,7 +351,8 @@ Params read_params(const double* p) {
     for (int a = 0; a < 3; ++a) q.uw[w][a] = p[13 + 4 * w + a];
     q.Tw[w] = p[13 + 4 * w + 3];
   }
-  for (int v = 0; v < 5; ++v) q.finf[v] = p[37 + v];
+  for (int w = 0; w < 6; ++w)
+    for (int v = 0; v < 5; ++v) q.finf[w][v] = p[37 + 5 * w + v];
   return q;
 }
 
@@ -765,7 +766,7 @@ void transform_state(const Mesh& m, const Params& P, const Xform& X, const T* q,
       n[ax] = pl >= 3 ? 1.0 : -1.0;
       T in[5];
       for (int v = 0; v < 5; ++v) in[v] = out[v];
-      farfield_state(P, in, n, out);
+      farfield_state(P, pl, in, n, out);
       continue;
     }
     const double* uw = P.uw[pl];
@@ -1212,15 +1213,16 @@ int residual(const Mesh& m, const Params& P, const T* Q, double dt, T* Lo, T* Lt
   return ST_OK;
 }
 
-// Far-field state at a boundary of outward unit normal n (Section 5.4: inlet and outlet by
-// Riemann invariants). From the interior state q and the far field, the invariants along n
+// Far-field state at a boundary plane of outward unit normal n (Section 5.4: inlet and outlet
+// by Riemann invariants). From the interior state q and the plane's far field, the invariants
+// along n
 // R+ = u_n + 2c/(gamma-1) (carried out of the domain) and R- = u_n - 2c/(gamma-1) (carried in)
 // are taken from the interior and the far field; the boundary u_n and c are their mean and
 // (gamma-1)/4 of their difference; the entropy p/rho^gamma and the tangential velocity come from
 // the side the flow comes from. Supersonic inflow takes the far field, supersonic outflow the
 // interior. Returns the conserved boundary state.
 template <class T>
-void farfield_state(const Params& P, const T* q, const double n[3], T* out) {
+void farfield_state(const Params& P, int plane, const T* q, const double n[3], T* out) {
   const double g = P.gamma, gm1 = g - 1.0;
   const T rho = q[0];
   T U[3], un = T(0.0), ke = T(0.0);
@@ -1231,8 +1233,8 @@ void farfield_state(const Params& P, const T* q, const double n[3], T* out) {
   }
   const T p = gm1 * (q[4] - 0.5 * rho * ke);
   const T c = sqrt(g * p / rho);
-  const double rinf = P.finf[0], pinf = P.finf[4];
-  const double* Uinf = P.finf + 1;
+  const double rinf = P.finf[plane][0], pinf = P.finf[plane][4];
+  const double* Uinf = P.finf[plane] + 1;
   double uninf = 0;
   for (int a = 0; a < 3; ++a) uninf += Uinf[a] * n[a];
   const double cinf = std::sqrt(g * pinf / rinf);
@@ -1290,7 +1292,7 @@ void wall_ghost(const Params& P, int kind, int plane, const T* v, const T g[5][3
   if (kind == 3) {  // far field: the characteristic boundary state, uniform (no gradient)
     double n[3] = {0, 0, 0};
     n[ax] = plane >= 3 ? 1.0 : -1.0;
-    farfield_state(P, v, n, vg);
+    farfield_state(P, plane, v, n, vg);
     for (int r = 0; r < 5; ++r)
       for (int b = 0; b < 3; ++b) gg[r][b] = T(0.0);
     return;

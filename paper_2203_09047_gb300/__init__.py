@@ -35,7 +35,7 @@ class gks_params(ctypes.Structure):
                 ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int),
                 ("T_ref", ctypes.c_double), ("mu_pow", ctypes.c_double),
                 ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6),
-                ("farfield", ctypes.c_double * 5)]
+                ("farfield", (ctypes.c_double * 5) * 6)]
 
 
 class GksError(RuntimeError):
@@ -140,10 +140,12 @@ def gks_params_default(**overrides) -> gks_params:
             v = np.asarray(v, dtype=np.float64).reshape(6)
             for w in range(6):
                 p.wall_T[w] = float(v[w])
-        elif k == "farfield":
-            v = np.asarray(v, dtype=np.float64).reshape(5)
-            for j in range(5):
-                p.farfield[j] = float(v[j])
+        elif k == "farfield":  # one state for every plane, or [6][5]
+            v = np.asarray(v, dtype=np.float64)
+            v = np.broadcast_to(v, (6, 5)) if v.size == 5 else v.reshape(6, 5)
+            for w in range(6):
+                for j in range(5):
+                    p.farfield[w][j] = float(v[w, j])
         else:
             setattr(p, k, v)
     return p

@@ -153,7 +153,6 @@ KParams<R> kparams(const gks_params& p) {
   k.weno_pow = p.weno_pow;
   k.T_ref = (R)p.T_ref;
   k.mu_pow = (R)p.mu_pow;
-  for (int v = 0; v < 5; ++v) k.finf[v] = (R)p.farfield[v];
   return k;
 }
 
@@ -393,11 +392,14 @@ bool valid_params(const gks_params* p, std::string& why) {
       why = "wall velocity and temperature must be finite";
       return false;
     }
-  if (!(p->farfield[0] > 0.0 && p->farfield[4] > 0.0 && std::isfinite(p->farfield[1]) &&
-        std::isfinite(p->farfield[2]) && std::isfinite(p->farfield[3]))) {
-    why = "the far-field state needs rho > 0, p > 0 and a finite velocity";
-    return false;
-  }
+  for (int w = 0; w < 6; ++w)
+    if (!(p->farfield[w][0] > 0.0 && p->farfield[w][4] > 0.0 &&
+          std::isfinite(p->farfield[w][0]) && std::isfinite(p->farfield[w][4]) &&
+          std::isfinite(p->farfield[w][1]) && std::isfinite(p->farfield[w][2]) &&
+          std::isfinite(p->farfield[w][3]))) {
+      why = "a far-field state needs rho > 0, p > 0 and a finite velocity";
+      return false;
+    }
   if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
   if (!(p->weno_eps > 0.0)) { why = "weno_eps must be > 0"; return false; }
   if (p->weno_pow < 1 || p->weno_pow > 4) { why = "weno_pow must be 1..4"; return false; }
@@ -472,9 +474,11 @@ void gks_params_default(gks_params* p) {
     p->wall_u[w][0] = p->wall_u[w][1] = p->wall_u[w][2] = 0.0;
     p->wall_T[w] = 0.0;
   }
-  p->farfield[0] = 1.0;
-  p->farfield[1] = p->farfield[2] = p->farfield[3] = 0.0;
-  p->farfield[4] = 1.0 / 1.4;
+  for (int w = 0; w < 6; ++w) {
+    p->farfield[w][0] = 1.0;
+    p->farfield[w][1] = p->farfield[w][2] = p->farfield[w][3] = 0.0;
+    p->farfield[w][4] = 1.0 / 1.4;
+  }
 }
 
 gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
@@ -577,13 +581,15 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
       return GKS_E_MESH;
     }
     if ((e = supload(s, &m.t_idx, tidx)) != cudaSuccess) return bad("upload");
-    std::vector<double> w64(24);
-    std::vector<float> w32(24);
+    std::vector<double> w64(6 * kPlaneStride, 0.0);
+    std::vector<float> w32(6 * kPlaneStride);
     for (int w = 0; w < 6; ++w) {
-      for (int a = 0; a < 3; ++a) w64[4 * w + a] = p->wall_u[w][a];
-      w64[4 * w + 3] = p->wall_T[w];
+      double* t = w64.data() + kPlaneStride * w;
+      for (int a = 0; a < 3; ++a) t[a] = p->wall_u[w][a];
+      t[3] = p->wall_T[w];
+      for (int v = 0; v < 5; ++v) t[4 + v] = p->farfield[w][v];
     }
-    for (int k = 0; k < 24; ++k) w32[k] = (float)w64[k];
+    for (size_t k = 0; k < w64.size(); ++k) w32[k] = (float)w64[k];
     if ((e = supload(s, &m.wall64, w64)) != cudaSuccess) return bad("upload");
     if ((e = supload(s, &m.wall32, w32)) != cudaSuccess) return bad("upload");
     m.ng = (int64_t)gsrc.size();

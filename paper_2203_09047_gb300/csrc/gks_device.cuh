@@ -96,7 +96,8 @@ struct DevMesh {
   // of each axis (2 bits per axis)
   uint8_t* g_chain = nullptr;
   int bcs = 0;
-  // no-slip wall planes (axis + 3 side): velocity and temperature, [6][4] in FP64 and FP32
+  // boundary planes (axis + 3 side): wall velocity and temperature, far-field state,
+  // [6][kPlaneStride] in FP64 and FP32 (see WallData)
   double* wall64 = nullptr;
   float* wall32 = nullptr;
 };
@@ -136,8 +137,7 @@ struct KParams {
   int flux_mode, tau_model;
   R weno_gamma, weno_eps;
   int weno_pow;
-  R T_ref, mu_pow;  // power-law viscosity (the wall planes live in DevMesh::wall64/wall32)
-  R finf[5];        // far-field state rho, U, V, W, p
+  R T_ref, mu_pow;  // power-law viscosity (the boundary planes live in DevMesh::wall64/wall32)
 };
 
 // ---- precompute (gks_geom.cu) -------------------------------------------------------------

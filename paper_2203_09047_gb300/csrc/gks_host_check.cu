@@ -8,7 +8,7 @@
 namespace {
 gks::FluxParams<double> params_from(const double* p) {
   // p = {gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr, T_ref, mu_pow,
-  //      wall_u[6][3], wall_T[6], farfield[5]}
+  //      wall_u[6][3], wall_T[6], farfield[6][5]}
   gks::FluxParams<double> P;
   P.gamma = p[0];
   P.K = (5.0 - 3.0 * p[0]) / (p[0] - 1.0);
@@ -20,16 +20,16 @@ gks::FluxParams<double> params_from(const double* p) {
   P.pr_fix = 1.0 / p[6] - 1.0;
   P.T_ref = p[7];
   P.mu_pow = p[8];
-  for (int v = 0; v < 5; ++v) P.finf[v] = p[33 + v];
   return P;
 }
 // the wall plane of `code` from p's wall_u[6][3], wall_T[6]
 gks::WallData<double> wall_from(const double* p, int code) {
   gks::WallData<double> d;
-  if (code >= 6 && code < 12) {
-    const int w = code - 6;
+  if (code >= 6) {
+    const int w = code % 6;
     for (int a = 0; a < 3; ++a) d.uw[a] = p[9 + 3 * w + a];
     d.Tw = p[27 + w];
+    for (int v = 0; v < 5; ++v) d.finf[v] = p[33 + 5 * w + v];
   }
   return d;
 }

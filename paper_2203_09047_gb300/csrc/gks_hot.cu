@@ -1026,14 +1026,14 @@ __global__ void __launch_bounds__(128) k_ghost_fill(int64_t nc, int64_t ng,
       if (kind == 1) {
         q[1 + ax] = -q[1 + ax];
       } else if (kind == 2) {
-        const R* t = wall_tab + 4 * w;
+        const R* t = wall_tab + kPlaneStride * w;
         const R um = t[0] * q[1] + t[1] * q[2] + t[2] * q[3];
         q[4] = q[4] + R(2) * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]) * q[0] - R(2) * um;
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[1 + a] = R(2) * t[a] * q[0] - q[1 + a];
       } else {
         R o[5];
-        farfield_state(P, ax, w >= 3 ? R(1) : R(-1), q, o);
+        farfield_state(P, wall_tab + kPlaneStride * w + 4, ax, w >= 3 ? R(1) : R(-1), q, o);
 #pragma unroll
         for (int v = 0; v < 5; ++v) q[v] = o[v];
       }

@@ -35,6 +35,9 @@ inline int wall_axis(int code) { return code % 3; }
 inline int wall_plane(int code) { return code % 6; }
 inline bool wall_noslip(int code) { return code >= 6 && code < 12; }
 inline bool wall_farfield(int code) { return code >= 12; }
+// Values per boundary plane in the device plane table: wall velocity (3), wall temperature,
+// far-field state (5), padding.
+constexpr int kPlaneStride = 12;
 
 // Host-side mesh after topology, stencil and ordering work. Cells and faces are in the
 // internal (Morton) order; perm maps internal cell -> caller cell.

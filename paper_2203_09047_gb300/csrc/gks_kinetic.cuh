@@ -6,6 +6,8 @@
 
 #include <cmath>
 
+#include "gks_internal.h"
+
 namespace gks {
 
 #define GKS_HD __host__ __device__ __forceinline__
@@ -405,26 +407,28 @@ struct FluxParams {
   int full, tau_model;
   R pr_fix = R(0);  // 1/Pr - 1 (heat-flux correction of the smooth flux; 0 for the BGK value)
   R T_ref = R(1), mu_pow = R(0.7);  // power law mu (T / T_ref)^mu_pow (collision time 3)
-  R finf[5] = {R(1), R(0), R(0), R(0), R(1.0 / 1.4)};  // far field: rho, U, V, W, p
 };
 
-// One no-slip wall plane: velocity and temperature (<= 0: adiabatic). The kernels read it from a
-// [6][4] device table (plane axis + 3 side) only at wall faces, so that the parameter block
+// One boundary plane: no-slip wall velocity and temperature (<= 0: adiabatic), far-field state
+// (rho, U, V, W, p). The kernels read it from a [6][kPlaneStride] device table (plane axis +
+// 3 side: uw[3], Tw, finf[5], padding) only at boundary faces, so that the parameter block
 // holds no array indexed at run time.
 template <class R>
 struct WallData {
   R uw[3] = {R(0), R(0), R(0)};
   R Tw = R(0);
+  R finf[5] = {R(1), R(0), R(0), R(0), R(1)};
 };
 template <class R>
 GKS_HD WallData<R> wall_data(const R* table, int code) {
   WallData<R> d;
-  if (code >= 6 && code < 12) {
-    const R* t = table + 4 * (code - 6);
-    d.uw[0] = t[0];
-    d.uw[1] = t[1];
-    d.uw[2] = t[2];
+  if (code >= 6) {
+    const R* t = table + kPlaneStride * (code % 6);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) d.uw[a] = t[a];
     d.Tw = t[3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) d.finf[v] = t[4 + v];
   }
   return d;
 }
@@ -443,7 +447,6 @@ inline FluxParams<R> flux_params(const KP<R>& p) {
   fp.pr_fix = p.pr_fix;
   fp.T_ref = p.T_ref;
   fp.mu_pow = p.mu_pow;
-  for (int v = 0; v < 5; ++v) fp.finf[v] = p.finf[v];
   return fp;
 }
 
@@ -463,15 +466,16 @@ GKS_HD R collision_time(const FluxParams<R>& P, R p0, R ir0, R dp, R dt) {
 // entropy p/rho^gamma and tangential velocity from the upwind side; supersonic inflow takes the
 // far field, supersonic outflow q. Conserved variables in and out.
 template <class R>
-GKS_HD void farfield_state(const FluxParams<R>& P, int ax, R sg, const R q[5], R out[5]) {
+GKS_HD void farfield_state(const FluxParams<R>& P, const R finf[5], int ax, R sg, const R q[5],
+                           R out[5]) {
   const R g = P.gamma, gm1 = P.gamma - R(1);
   const R ir = R(1) / q[0];
   const R U[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
   const R p = gm1 * (q[4] - R(0.5) * (q[1] * U[0] + q[2] * U[1] + q[3] * U[2]));
   const R c = k_sqrt(g * p * ir);
   const R un = sg * U[ax];
-  const R rinf = P.finf[0], pinf = P.finf[4];
-  const R Uinf[3] = {P.finf[1], P.finf[2], P.finf[3]};
+  const R rinf = finf[0], pinf = finf[4];
+  const R Uinf[3] = {finf[1], finf[2], finf[3]};
   const R uninf = sg * Uinf[ax];
   const R cinf = k_sqrt(g * pinf / rinf);
   R rb, pb, Ub[3];
@@ -513,7 +517,7 @@ GKS_HD void wall_ghost(const FluxParams<R>& P, int code, const WallData<R>& wd, 
                        const R g[5][3], R vg[5], R gg[5][3]) {
   const int ax = code % 3;
   if (code >= 12) {  // far field: the characteristic state, uniform
-    farfield_state(P, ax, (code % 6) >= 3 ? R(1) : R(-1), v, vg);
+    farfield_state(P, wd.finf, ax, (code % 6) >= 3 ? R(1) : R(-1), v, vg);
 #pragma unroll
     for (int r = 0; r < 5; ++r)
 #pragma unroll

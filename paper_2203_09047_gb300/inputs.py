@@ -99,8 +99,9 @@ def _signed_vol(x, a, b, c, d):
 
 
 def layered_box_mesh(n: int, layers="hybrid8", lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0),
-                     jitter: float = 0.1, seed: int = 1, bc=(BC_PERIODIC,) * 3):
-    """The layered hybrid box mesh described in the module docstring.
+                     jitter: float = 0.1, seed: int = 1, bc=(BC_PERIODIC,) * 3, shape=None):
+    """The layered hybrid box mesh described in the module docstring: n z-layers of n x n
+    cubes, or of shape = (nx, ny) cubes.
 
     Returns a dict with
         xyz        float64 [n_nodes, 3]
@@ -113,26 +114,28 @@ def layered_box_mesh(n: int, layers="hybrid8", lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0,
         layers = layer_pattern(layers, n)
     if len(layers) != n:
         raise ValueError("need one layer kind per z-layer")
+    nx, ny = (n, n) if shape is None else (int(shape[0]), int(shape[1]))
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
-    h = (hi - lo) / n
-    m = n + 1
-    ii, jj, kk = np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij")
+    counts = np.array([nx, ny, n])
+    h = (hi - lo) / counts
+    mx, my, mz = nx + 1, ny + 1, n + 1
+    ii, jj, kk = np.meshgrid(np.arange(mx), np.arange(my), np.arange(mz), indexing="ij")
     lat = np.stack([ii.transpose(2, 1, 0).ravel(), jj.transpose(2, 1, 0).ravel(),
-                    kk.transpose(2, 1, 0).ravel()], axis=1)  # id = i + m*(j + m*k)
+                    kk.transpose(2, 1, 0).ravel()], axis=1)  # id = i + mx*(j + my*k)
     xyz = [lo[None, :] + lat * h[None, :]]
-    interior = np.all((lat > 0) & (lat < n), axis=1)
+    interior = np.all((lat > 0) & (lat < counts[None, :]), axis=1)
 
     def lid(i, j, k):
-        return i + m * (j + m * k)
+        return i + mx * (j + my * k)
 
-    n_lat = m ** 3
+    n_lat = mx * my * mz
     centre = {}
     centres = []
     for k, kind in enumerate(layers):
         if kind in ("trans", "transm"):
-            for j in range(n):
-                for i in range(n):
+            for j in range(ny):
+                for i in range(nx):
                     centre[(i, j, k)] = n_lat + len(centres)
                     centres.append(lo + (np.array([i, j, k]) + 0.5) * h)
     if centres:
@@ -144,8 +147,8 @@ def layered_box_mesh(n: int, layers="hybrid8", lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0,
         u = uniform01(seed, (3 * ids[:, None] + np.arange(3, dtype=np.uint64)[None, :]).ravel())
         xyz[ids] += ((2.0 * u - 1.0) * jitter).reshape(-1, 3) * h[None, :]
 
-    # vectorised over the n x n cubes of each layer (x fastest, then y)
-    jj2, ii2 = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    # vectorised over the nx x ny cubes of each layer (x fastest, then y)
+    jj2, ii2 = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
     ii2, jj2 = ii2.ravel(), jj2.ravel()
     kuhn = _kuhn_paths()
     blocks_t, blocks_n = [], []
@@ -208,7 +211,7 @@ def layered_box_mesh(n: int, layers="hybrid8", lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0,
     cell_nodes = np.ascontiguousarray(nodes, dtype=np.int64)
     return {"xyz": np.ascontiguousarray(xyz), "cell_type": cell_type, "cell_nodes": cell_nodes,
             "bc": tuple(int(b) for b in bc), "lo": tuple(float(v) for v in lo),
-            "hi": tuple(float(v) for v in hi), "n": n, "layers": tuple(layers)}
+            "hi": tuple(float(v) for v in hi), "n": n, "shape": (nx, ny), "layers": tuple(layers)}
 
 
 def mesh_summary(mesh) -> dict:

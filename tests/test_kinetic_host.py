@@ -28,11 +28,12 @@ def lib():
 def _hp(mode, tau_model, mu=2e-3, Pr=1.0, T_ref=T_REF, mu_pow=0.7, wall_u=None, wall_T=None,
         farfield=(1.0, 0.0, 0.0, 0.0, 1.0 / 1.4)):
     """Parameter vector of the host entries: gamma, mu, tau_eps, tau_C, flux_mode, tau_model, Pr,
-    T_ref, mu_pow, wall_u[6][3], wall_T[6], farfield[5]."""
+    T_ref, mu_pow, wall_u[6][3], wall_T[6], farfield[6][5]."""
     wu = np.zeros(18) if wall_u is None else np.asarray(wall_u, dtype=np.float64).ravel()
     wT = np.zeros(6) if wall_T is None else np.asarray(wall_T, dtype=np.float64).ravel()
-    return np.concatenate([[1.4, mu, 0.01, 1.0, mode, tau_model, Pr, T_ref, mu_pow], wu, wT,
-                           farfield])
+    ff = np.asarray(farfield, dtype=np.float64)
+    ff = np.broadcast_to(ff, (6, 5)).ravel() if ff.size == 5 else ff.ravel()
+    return np.concatenate([[1.4, mu, 0.01, 1.0, mode, tau_model, Pr, T_ref, mu_pow], wu, wT, ff])
 
 
 def _state(rng):

@@ -241,3 +241,31 @@ def test_farfield_box_keeps_the_free_stream(finf):
         S.step(2e-3, 3)
         err = np.abs(S.get_state().cpu().numpy() - Q).max()
         assert err < tol * np.abs(Q).max(), err
+
+
+@pytest.mark.parametrize("layers", [("hex",) * 4, ("tet",) * 4, ("hex", "trans", "tet", "transm")])
+def test_riemann_tube_with_farfield_ends_matches_oracle(layers):
+    """The Riemann-problem setup of Section 5 at h = 1/40: [0,1] x [0,0.1] x [0,0.1], far-field
+    x ends holding the left and right Lax states (one state per plane), slip y and z walls."""
+    m = I.layered_box_mesh(4, layers, lo=(0, 0, 0), hi=(1, 0.1, 0.1), bc=(3, 1, 1), jitter=0.05,
+                           shape=(40, 4))
+    om = oracle.Mesh(m)
+    x = I.vertex_mean(m)
+    left = x[:, 0] < 0.5
+    U0 = np.zeros((len(left), 3))
+    U0[:, 0] = np.where(left, 0.698, 0.0)
+    Q = np.ascontiguousarray(I.primitive_to_conserved(np.where(left, 0.445, 0.5), U0,
+                                                      np.where(left, 3.528, 0.571)))
+    far = np.tile(np.array([1.0, 0.0, 0.0, 0.0, 1.0]), (6, 1))
+    far[0] = (0.445, 0.698, 0.0, 0.0, 3.528)
+    far[3] = (0.5, 0.0, 0.0, 0.0, 0.571)
+    p = dict(flux_mode=1, tau_model=1)
+    P = oracle.params_vec(farfield=far, **p)
+    Lo, Lto = om.residual(P, Q, 1e-3)
+    S = gks.Solver(m, farfield=far, **p)
+    L, Lt = S.residual(Q, 1e-3)
+    assert rel(L.cpu(), Lo) < FP64_TOL and rel(Lt.cpu(), Lto) < FP64_TOL
+    S.set_state(Q)
+    dt = S.max_dt(0.4)
+    S.step(dt, 4)
+    assert rel(S.get_state().cpu(), om.step(P, Q, dt, 4)) < FP64_TOL
