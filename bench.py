@@ -207,7 +207,7 @@ _LID[4][0] = 0.15  # the upper y plane moves along x at Ma 0.15 (c = 1)
 IMPLICIT_CASES = [
     # name, cubes, layers box, bc, params, paper (cells, ms per step) for context
     ("cavity", 32, ((0, 0, 0), (1, 1, 1)), (2, 2, 2),
-     dict(flux_mode=0, tau_model=2, mu=0.15 / 1000.0, wall_u=_LID, wall_T=[1.0 / 1.4] * 6),
+     dict(flux_mode=1, tau_model=2, mu=0.15 / 1000.0, wall_u=_LID, wall_T=[1.0 / 1.4] * 6),
      (102400, 97.0)),
     ("sphere_like", 48, ((0, 0, 0), (2, 2, 2)), (0, 0, 0),
      dict(flux_mode=1, tau_model=1), (462673, 1093.0)),
