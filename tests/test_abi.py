@@ -41,7 +41,8 @@ def test_params_default(lib):
 
 @pytest.mark.parametrize("n,layers,bc", [(8, "hybrid8", (0, 0, 0)), (4, "hex", (0, 0, 0)),
                                          (4, "tet", (0, 0, 0)), (8, "hybrid8", (1, 1, 1)),
-                                         (8, "hybrid8", (0, 1, 0))])
+                                         (8, "hybrid8", (0, 1, 0)), (8, "hybrid8", (2, 2, 2)),
+                                         (4, "tet", (3, 1, 2)), (4, "hex", (3, 3, 3))])
 def test_mesh_counts_match_oracle(lib, n, layers, bc):
     m = I.layered_box_mesh(n, layers, bc=bc)
     h = gks.gks_mesh_create(m["xyz"], m["cell_type"], m["cell_nodes"], m["bc"], m["lo"], m["hi"])
@@ -72,3 +73,30 @@ def test_mesh_errors(lib):
     with pytest.raises(gks.GksError) as e:
         gks.gks_mesh_create(m["xyz"], m["cell_type"], nodes, m["bc"], m["lo"], m["hi"])
     assert e.value.status == gks.GKS_E_INVAL
+
+
+def test_invalid_parameters_are_rejected_before_any_device_work(lib):
+    """gks_init validates its parameters first (no CUDA call is made for a rejected set)."""
+    m = I.layered_box_mesh(4, "hex", bc=(3, 2, 1))
+    h = gks.gks_mesh_create(m["xyz"], m["cell_type"], m["cell_nodes"], m["bc"], m["lo"], m["hi"])
+    try:
+        far_bad = np.tile([1.0, 0.0, 0.0, 0.0, 1.0], (6, 1))
+        far_bad[3, 4] = -1.0
+        wall_bad = np.zeros((6, 3))
+        wall_bad[4, 0] = np.nan
+        for bad in (dict(tau_model=3, T_ref=0.0), dict(tau_model=4), dict(farfield=far_bad),
+                    dict(wall_u=wall_bad), dict(wall_T=[0, 0, 0, 0, np.inf, 0])):
+            with pytest.raises(gks.GksError) as e:
+                gks.gks_init(h, gks.gks_params_default(**bad))
+            assert e.value.status == gks.GKS_E_INVAL, bad
+    finally:
+        gks.gks_mesh_destroy(h)
+
+
+def test_wall_and_farfield_parameter_defaults(lib):
+    p = gks.gks_params_default()
+    assert p.T_ref == 1.0 and p.mu_pow == 0.7
+    assert all(p.wall_T[w] == 0.0 and list(p.wall_u[w]) == [0.0, 0.0, 0.0] for w in range(6))
+    assert all(list(p.farfield[w]) == [1.0, 0.0, 0.0, 0.0, 1.0 / 1.4] for w in range(6))
+    q = gks.gks_params_default(farfield=(1.2, 0.1, 0.0, 0.0, 0.9))
+    assert all(list(q.farfield[w]) == [1.2, 0.1, 0.0, 0.0, 0.9] for w in range(6))
