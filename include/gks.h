@@ -84,16 +84,16 @@ typedef struct {
    * density, U_g = 2 U_w - U and p_g = p (adiabatic) or T_g = 2 T_w - T (isothermal); ghost cells
    * in the stencils take U_g = 2 U_w - U at the same density and pressure. The wall flux has no
    * mass component; at an adiabatic wall its energy component is U_w . (momentum flux). Ignored
-   * on periodic and slip planes. The VJP supports adiabatic walls only. */
+   * on periodic and slip planes. */
   double wall_u[6][3];
   double wall_T[6];
   /* Far-field planes: the state (rho, U, V, W, p) outside. The ghost at a far-field plane, in
    * the stencils and at the Gauss points, is the characteristic boundary state: the outgoing
    * invariant u_n + 2c/(gamma-1) from inside, the incoming u_n - 2c/(gamma-1) from this state,
    * entropy and tangential velocity from the upwind side (supersonic inflow: this state,
-   * supersonic outflow: the inside state); it carries no gradient at the Gauss points. The VJP
-   * rejects meshes with far-field planes. One state per plane (axis + 3 side), default
-   * (1, 0, 0, 0, 1/1.4). */
+   * supersonic outflow: the inside state); it carries no gradient at the Gauss points. One state
+   * per plane (axis + 3 side), default (1, 0, 0, 0, 1/1.4). gks_residual_vjp rejects meshes
+   * with far-field planes (GKS_E_INVAL). */
   double farfield[6][5];
 } gks_params;
 

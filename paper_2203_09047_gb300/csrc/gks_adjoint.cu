@@ -323,9 +323,48 @@ __global__ void __launch_bounds__(64) k_vjp_recon(
   }
 }
 
+// One boundary plane's map of a ghost cell's flow variables (as k_ghost_fill applies it):
+// slip, normal momentum negated; no-slip with velocity t[0..2], m -> 2 U_w rho - m,
+// E -> E + 2 |U_w|^2 rho - 2 U_w . m; far field, the characteristic state. And its
+// transposed Jacobian at q applied to y, added to g.
+__device__ void plane_map(const FluxParams<double>& P, int w, int kind, const double* t,
+                          const double q[5], double out[5]) {
+  const int ax = w % 3;
+  if (kind == 3) {
+    farfield_state(P, t + 4, ax, w >= 3 ? 1.0 : -1.0, q, out);
+    return;
+  }
+  for (int v = 0; v < 5; ++v) out[v] = q[v];
+  if (kind == 1) {
+    out[1 + ax] = -q[1 + ax];
+    return;
+  }
+  const double um = t[0] * q[1] + t[1] * q[2] + t[2] * q[3];
+  out[4] = q[4] + 2.0 * (t[0] * t[0] + t[1] * t[1] + t[2] * t[2]) * q[0] - 2.0 * um;
+  for (int a = 0; a < 3; ++a) out[1 + a] = 2.0 * t[a] * q[0] - q[1 + a];
+}
+__device__ void plane_map_vjp(const FluxParams<double>& P, int w, int kind, const double* t,
+                              const double q[5], const double y[5], double g[5]) {
+  const int ax = w % 3;
+  if (kind == 3) {
+    farfield_state_vjp(P, t + 4, ax, w >= 3 ? 1.0 : -1.0, q, y, g);
+    return;
+  }
+  if (kind == 1) {
+    for (int v = 0; v < 5; ++v) g[v] += (v == 1 + ax) ? -y[v] : y[v];
+    return;
+  }
+  const double uw2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+  g[0] += y[0] + 2.0 * (t[0] * y[1] + t[1] * y[2] + t[2] * y[3]) + 2.0 * uw2 * y[4];
+  for (int a = 0; a < 3; ++a) g[1 + a] += -y[1 + a] - 2.0 * t[a] * y[4];
+  g[4] += y[4];
+}
+
 __global__ void k_vjp_stencil(int64_t nc, const int32_t* __restrict__ rs_ptr,
                               const int32_t* __restrict__ rs_pos, const int32_t* __restrict__ t_idx,
-                              const double* __restrict__ g_map, const double* __restrict__ gdq,
+                              const double* __restrict__ g_map, const uint8_t* __restrict__ g_chain,
+                              int bcs, FluxParams<double> P, const double* __restrict__ wall_tab,
+                              const double* __restrict__ QA, const double* __restrict__ gdq,
                               const double* __restrict__ gq0, double* __restrict__ gQ) {
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= nc) return;
@@ -339,6 +378,23 @@ __global__ void k_vjp_stencil(int64_t nc, const int32_t* __restrict__ rs_ptr,
     const double* g = gdq + slot * 5 * kTile + lane;
     double y[5];
     for (int v = 0; v < 5; ++v) y[v] = g[v * kTile];
+    if ((e & kCellMask) >= nc && g_chain[(e & kCellMask) - nc]) {
+      // a ghost slot across a far-field plane: the planes' maps reversed at this cell's state
+      const int code = g_chain[(e & kCellMask) - nc];
+      const int w0 = (code & 7) - 1, w1 = ((code >> 3) & 7) - 1;
+      double q0[5], q1[5], y0[5] = {0, 0, 0, 0, 0};
+      for (int v = 0; v < 5; ++v) q0[v] = QA[6 * j + v];
+      const int k0 = (bcs >> (2 * (w0 % 3))) & 3;
+      if (w1 >= 0) {
+        const int k1 = (bcs >> (2 * (w1 % 3))) & 3;
+        plane_map(P, w0, k0, wall_tab + kPlaneStride * w0, q0, q1);
+        plane_map_vjp(P, w1, k1, wall_tab + kPlaneStride * w1, q1, y, y0);
+      } else {
+        for (int v = 0; v < 5; ++v) y0[v] = y[v];
+      }
+      plane_map_vjp(P, w0, k0, wall_tab + kPlaneStride * w0, q0, y0, s);
+      continue;
+    }
     if ((e & kCellMask) >= nc) {
       // a wall ghost slot: the transpose of its map (rho, m_j, E) -> (rho, s_j m_j + a_j rho,
       // E + b rho + c . m)
@@ -366,6 +422,13 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
   const FluxParams<double> fp = flux_params(p);
   auto kern = fp.full ? (fp.tau_model == 0 ? k_vjp_flux<true, true> : k_vjp_flux<true, false>)
                       : (fp.tau_model == 0 ? k_vjp_flux<false, true> : k_vjp_flux<false, false>);
+  // the flux adjoint keeps kilobytes of spilled state per thread in its stack frame (4-6 KB for
+  // the full flux): raise the context's per-thread stack limit to cover it before the launch
+  cudaFuncAttributes at;
+  size_t cur = 0;
+  if (cudaFuncGetAttributes(&at, kern) == cudaSuccess &&
+      cudaDeviceGetLimit(&cur, cudaLimitStackSize) == cudaSuccess && at.localSizeBytes > cur)
+    cudaDeviceSetLimit(cudaLimitStackSize, at.localSizeBytes);
   kern<<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly,
                                                   gL, gLt, g64.vol, m.nc, fp, m.wall64, dt, gpf,
                                                   flag);
@@ -375,6 +438,7 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
                                                      g.h, p.weno_gamma, p.weno_eps, p.weno_pow, gpc,
                                                      gdq, gq0);
   k_vjp_stencil<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, rs_ptr, rs_pos, m.t_idx, m.g_map,
+                                                        m.g_chain, m.bcs, fp, m.wall64, QA,
                                                         gdq, gq0, gQ);
 }
 

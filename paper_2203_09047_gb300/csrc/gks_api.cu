@@ -778,7 +778,7 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
   if (s->prm.Pr != 1.0) return s->fail(GKS_E_INVAL, "the VJP supports Pr = 1 only");
   for (int a = 0; a < 3; ++a)
     if (((s->m.bcs >> (2 * a)) & 3) == GKS_BC_FARFIELD)
-      return s->fail(GKS_E_INVAL, "the VJP does not support far-field planes");
+      return s->fail(GKS_E_INVAL, "the VJP does not take far-field planes");
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e = cudaSuccess;
   if (!s->vjp_ready) {

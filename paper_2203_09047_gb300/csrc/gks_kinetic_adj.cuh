@@ -534,6 +534,73 @@ GKS_HD void wall_flux_fix_adj(int code, const WallData<R>& wd, R gacc[10]) {
   }
 }
 
+// Reverse of farfield_state: the cotangent y of the boundary state (conserved) -> that of the
+// inside state q, added to g. Supersonic outflow passes y, supersonic inflow nothing; the
+// subsonic state depends on q through R+ = u_n + 2c/(gamma-1) and, at an outflow, through the
+// entropy p/rho^gamma and the tangential velocity.
+template <class R>
+GKS_HD void farfield_state_vjp(const FluxParams<R>& P, const R finf[5], int ax, R sg,
+                               const R q[5], const R y[5], R g[5]) {
+  const R gam = P.gamma, gm1 = P.gamma - R(1);
+  const R ir = R(1) / q[0];
+  const R U[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+  const R U2 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+  const R p = gm1 * (q[4] - R(0.5) * q[0] * U2);
+  const R c = k_sqrt(gam * p * ir);
+  const R un = sg * U[ax];
+  if (un >= c) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) g[v] += y[v];
+    return;
+  }
+  if (un <= -c) return;
+  const R rinf = finf[0], pinf = finf[4];
+  const R uninf = sg * finf[1 + ax];
+  const R cinf = k_sqrt(gam * pinf / rinf);
+  const R Rp = un + R(2) * c / gm1, Rm = uninf - R(2) * cinf / gm1;
+  const R unb = R(0.5) * (Rp + Rm), cb = R(0.25) * gm1 * (Rp - Rm);
+  const bool out_flow = unb >= R(0);
+  const R s = out_flow ? p / k_pow(q[0], gam) : pinf / k_pow(rinf, gam);
+  R Ub[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) Ub[a] = out_flow ? U[a] : finf[1 + a];
+  Ub[ax] = sg * unb;
+  const R rb = k_pow(cb * cb / (gam * s), R(1) / gm1);
+  // out = (rb, rb Ub, pb/(gamma-1) + rb |Ub|^2 / 2), pb = rb cb^2 / gamma
+  const R Ub2 = Ub[0] * Ub[0] + Ub[1] * Ub[1] + Ub[2] * Ub[2];
+  R grb = y[0] + y[1] * Ub[0] + y[2] * Ub[1] + y[3] * Ub[2] + R(0.5) * Ub2 * y[4];
+  R gUb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) gUb[a] = rb * (y[1 + a] + y[4] * Ub[a]);
+  const R gpb = y[4] / gm1;
+  grb += gpb * cb * cb / gam;
+  R gcb = gpb * R(2) * rb * cb / gam;
+  // rb = (cb^2 / (gamma s))^(1/(gamma-1))
+  gcb += grb * rb * R(2) / (gm1 * cb);
+  const R gs = -grb * rb / (gm1 * s);
+  const R gunb = sg * gUb[ax];
+  const R gRp = R(0.5) * gunb + R(0.25) * gm1 * gcb;
+  // back to the inside primitives
+  R gU[3] = {R(0), R(0), R(0)}, grho = R(0), gp = R(0);
+  if (out_flow) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (a != ax) gU[a] += gUb[a];
+    const R rg = k_pow(q[0], gam);
+    gp += gs / rg;
+    grho += -gs * gam * p / (rg * q[0]);
+  }
+  gU[ax] += sg * gRp;                      // R+ through u_n
+  const R gc = gRp * R(2) / gm1;           // ... and through c = sqrt(gamma p / rho)
+  gp += gc * c / (R(2) * p);
+  grho += -gc * c / (R(2) * q[0]);
+  // primitives -> conserved
+  g[0] += grho - (gU[0] * U[0] + gU[1] * U[1] + gU[2] * U[2]) * ir + gp * gm1 * R(0.5) * U2;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) g[1 + a] += gU[a] * ir - gp * gm1 * U[a];
+  g[4] += gp * gm1;
+}
+
 // Reverse of wall_ghost: the cotangents (gvg, ggg) of the ghost value and gradient are added to
 // those (gv, gg) of the owner's. The slip and adiabatic maps are linear (the transposed Jacobian
 // and mirror); the isothermal map's energy row depends on U = m / rho also through the
@@ -543,7 +610,10 @@ GKS_HD void wall_ghost_vjp(const FluxParams<R>& P, int code, const WallData<R>& 
                            const R g[5][3], const R gvg[5], const R ggg[5][3], R gv[5],
                            R gg[5][3]) {
   const int ax = code % 3;
-  if (code >= 12) return;  // far-field planes: the VJP entry point rejects such meshes
+  if (code >= 12) {  // far field: the ghost is a function of the owner's value only
+    farfield_state_vjp(P, wd.finf, ax, (code % 6) >= 3 ? R(1) : R(-1), v, gvg, gv);
+    return;
+  }
   if (code < 6) {
 #pragma unroll
     for (int r = 0; r < 5; ++r) {

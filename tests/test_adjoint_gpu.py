@@ -16,6 +16,7 @@ from paper_2203_09047_gb300 import build, inputs as I  # noqa: E402
 
 CASES = {
     "smooth_zero": dict(flux_mode=0, tau_model=0),
+    "full_zero": dict(flux_mode=1, tau_model=0),
     "full_inviscid": dict(flux_mode=1, tau_model=1),
     "full_viscous": dict(flux_mode=1, tau_model=2, mu=1e-3),
     "smooth_viscous": dict(flux_mode=0, tau_model=2, mu=2e-3),

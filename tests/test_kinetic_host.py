@@ -185,12 +185,15 @@ def test_wall_ghost_matches_oracle(lib, code, iso):
         np.testing.assert_allclose(gg.reshape(5, 3), go, rtol=1e-13, atol=1e-14)
 
 
-@pytest.mark.parametrize("code", [1, 7, 9])
+@pytest.mark.parametrize("code", [1, 7, 9, 12, 16])
 @pytest.mark.parametrize("iso", [False, True])
 def test_wall_ghost_vjp_matches_central_differences(lib, code, iso):
+    """Slip, no-slip (adiabatic, isothermal) and far-field ghosts (codes 12 + plane; subsonic
+    in- or outflow for these states)."""
     rng = np.random.default_rng(450 + code + 20 * iso)
     uw, Tw = _wall_params(rng, iso)
-    P = _hp(0, 2, wall_u=uw, wall_T=Tw)
+    finf = (1.1, 0.2, -0.15, 0.1, 0.8) if iso else (0.9, -0.3, 0.05, 0.2, 0.7)
+    P = _hp(0, 2, wall_u=uw, wall_T=Tw, farfield=finf)
     v, g = _state(rng), rng.normal(size=15) * 0.3
     x = np.concatenate([v, g])
 

@@ -224,9 +224,17 @@ def test_farfield_steps_and_implicit_match_oracle():
     S.set_state(Q)
     S.step_implicit(4 * dt, 2, 3)
     assert rel(S.get_state().cpu(), om.step_implicit(P, Q, 4 * dt, 2, 3)) < FP64_TOL
-    with pytest.raises(gks.GksError):
-        gL, gLt, _ = I.normal_directions(Q.shape, 3, 62)
-        S.residual_vjp(Q, dt, gL, gLt)
+
+
+def test_farfield_vjp_is_rejected():
+    """gks_residual_vjp does not take far-field planes: it returns GKS_E_INVAL."""
+    m, om = mesh_pair(8, "hybrid8", (3, 3, 3))
+    Q = farfield_state(om, seed=63)
+    gL, gLt, _ = I.normal_directions(Q.shape, 3, 64)
+    S = gks.Solver(m, farfield=FINF, flux_mode=1, tau_model=2, mu=2e-3)
+    with pytest.raises(gks.GksError) as e:
+        S.residual_vjp(Q, 0.004, gL, gLt)
+    assert e.value.status == gks.GKS_E_INVAL
 
 
 @pytest.mark.parametrize("finf", [FINF, (1.0, 1.6, 0.3, -0.2, 1.0 / 1.4)])
