@@ -25,8 +25,10 @@ struct PolyRef64 {
 };
 
 // kFull and kTau0 fix the flux form and a zero collision time at compile time (as in the forward
-// kernel), so that each instance holds only its own form's recomputed forward state.
-template <bool kFull, bool kTau0>
+// kernel), so that each instance holds only its own form's recomputed forward state. kWalls =
+// false is the instance for meshes without boundary planes (every face has two cells; no
+// boundary code compiled in), true the one that handles both kinds of face.
+template <bool kFull, bool kTau0, bool kWalls>
 __global__ void __launch_bounds__(128) k_vjp_flux(
     int64_t nf, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const double* __restrict__ fgp,
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
       gacc[q] = -gL[q * nc + o] * io;
       gacc[5 + q] = -gLt[q * nc + o] * io;
     }
-    if (nb >= 0) {
+    if (!kWalls || nb >= 0) {
       const double in = 1.0 / vol[nb];
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
@@ -75,10 +77,10 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
     const double w = fgp[9 * stride + gid];
     double vl[5], gl[5][3], vr[5], gr[5][3];
     eval_poly(PolyRef64{poly + (int64_t)kPolyStride * o}, dl, vl, gl);
-    if (nb >= 0) {
+    if (!kWalls || nb >= 0) {
       eval_poly(PolyRef64{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
     } else {
-      wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
+      wall_ghost<double, false>(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
     }
     double gvl[5] = {0, 0, 0, 0, 0}, gvr[5] = {0, 0, 0, 0, 0};
     double ggl[5][3], ggr[5][3];
@@ -88,9 +90,10 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
       for (int a = 0; a < 3; ++a) ggl[v][a] = ggr[v][a] = 0.0;
     if (gp_flux_global_vjp(P, vl, gl, vr, gr, n1, w, dt, gacc, gvl, ggl, gvr, ggr)) {
       // the wall's ghost is a function of the owner's value and gradient: fold its cotangent back
-      if (nb < 0) wall_ghost_vjp(P, wall, wall_data(wall_tab, wall), vl, gl, gvr, ggr, gvl, ggl);
+      if (kWalls && nb < 0)
+        wall_ghost_vjp(P, wall, wall_data(wall_tab, wall), vl, gl, gvr, ggr, gvl, ggl);
       eval_poly_adj(dl, gvl, ggl, go);
-      if (nb >= 0) eval_poly_adj(dr, gvr, ggr, gn);
+      if (!kWalls || nb >= 0) eval_poly_adj(dr, gvr, ggr, gn);
     } else {
       atomicOr(flag, kErrNonphysical);
     }
@@ -420,8 +423,13 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
                 double dt, double* gpf, double* gpc, double* gdq, double* gq0, double* gQ,
                 const int32_t* rs_ptr, const int32_t* rs_pos, int* flag, cudaStream_t st) {
   const FluxParams<double> fp = flux_params(p);
-  auto kern = fp.full ? (fp.tau_model == 0 ? k_vjp_flux<true, true> : k_vjp_flux<true, false>)
-                      : (fp.tau_model == 0 ? k_vjp_flux<false, true> : k_vjp_flux<false, false>);
+  using Kern = decltype(&k_vjp_flux<true, true, true>);
+  const Kern tab[2][2][2] = {
+      {{k_vjp_flux<false, false, false>, k_vjp_flux<false, false, true>},
+       {k_vjp_flux<false, true, false>, k_vjp_flux<false, true, true>}},
+      {{k_vjp_flux<true, false, false>, k_vjp_flux<true, false, true>},
+       {k_vjp_flux<true, true, false>, k_vjp_flux<true, true, true>}}};
+  const Kern kern = tab[fp.full ? 1 : 0][fp.tau_model == 0 ? 1 : 0][m.bcs != 0 ? 1 : 0];
   // the flux adjoint keeps kilobytes of spilled state per thread in its stack frame (4-6 KB for
   // the full flux): raise the context's per-thread stack limit to cover it before the launch
   cudaFuncAttributes at;

@@ -117,7 +117,10 @@ extern "C" void gks_wall_ghost_host(const double* p, int code, const double* v, 
     gv[r] = 0.0;
     for (int b = 0; b < 3; ++b) Y[r][b] = ggg[3 * r + b];
   }
-  gks::wall_ghost_vjp(P, code, wd, v, G, gvg, Y, gv, A);
+  if (code >= 12)  // far field: a function of the owner's value only
+    gks::farfield_state_vjp(P, wd.finf, code % 3, (code % 6) >= 3 ? 1.0 : -1.0, v, gvg, gv);
+  else
+    gks::wall_ghost_vjp(P, code, wd, v, G, gvg, Y, gv, A);
   for (int r = 0; r < 5; ++r)
     for (int b = 0; b < 3; ++b) gga[3 * r + b] = A[r][b];
 }

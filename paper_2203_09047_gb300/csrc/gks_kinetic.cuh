@@ -427,8 +427,10 @@ GKS_HD WallData<R> wall_data(const R* table, int code) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) d.uw[a] = t[a];
     d.Tw = t[3];
+    if (code >= 12) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) d.finf[v] = t[4 + v];
+      for (int v = 0; v < 5; ++v) d.finf[v] = t[4 + v];
+    }
   }
   return d;
 }
@@ -512,11 +514,12 @@ GKS_HD void farfield_state(const FluxParams<R>& P, const R finf[5], int ax, R sg
 // rho_g = rho, m_g = 2 U_w rho - m and E_g = E + 2 |U_w|^2 rho - 2 U_w . m (adiabatic, p_g = p)
 // or E_g = 2 rho T_w / (gamma-1) - E + |m|^2/rho + 2 |U_w|^2 rho - 2 U_w . m (isothermal,
 // T_g = 2 T_w - T); the gradient is mapped by the Jacobian of that map.
-template <class R>
+// kFar = false leaves the far-field branch out (for callers that never see far-field planes).
+template <class R, bool kFar = true>
 GKS_HD void wall_ghost(const FluxParams<R>& P, int code, const WallData<R>& wd, const R v[5],
                        const R g[5][3], R vg[5], R gg[5][3]) {
   const int ax = code % 3;
-  if (code >= 12) {  // far field: the characteristic state, uniform
+  if (kFar && code >= 12) {  // far field: the characteristic state, uniform
     farfield_state(P, wd.finf, ax, (code % 6) >= 3 ? R(1) : R(-1), v, vg);
 #pragma unroll
     for (int r = 0; r < 5; ++r)

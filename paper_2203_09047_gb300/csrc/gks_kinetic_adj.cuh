@@ -610,10 +610,9 @@ GKS_HD void wall_ghost_vjp(const FluxParams<R>& P, int code, const WallData<R>& 
                            const R g[5][3], const R gvg[5], const R ggg[5][3], R gv[5],
                            R gg[5][3]) {
   const int ax = code % 3;
-  if (code >= 12) {  // far field: the ghost is a function of the owner's value only
-    farfield_state_vjp(P, wd.finf, ax, (code % 6) >= 3 ? R(1) : R(-1), v, gvg, gv);
-    return;
-  }
+  // far-field planes: the ghost is farfield_state of the owner's value only (its reverse is
+  // farfield_state_vjp); gks_residual_vjp does not take such meshes, so the kernel leaves it out
+  if (code >= 12) return;
   if (code < 6) {
 #pragma unroll
     for (int r = 0; r < 5; ++r) {
