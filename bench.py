@@ -182,6 +182,20 @@ def reference_arm(args):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def job_rate(ms_local, units_local, world, dist=None, device="cuda"):
+    """Whole-job throughput of N independent replicas: the slowest rank's time (max over
+    ranks) and the units all ranks processed divided by it. Returns (max ms, units per s)."""
+    import torch
+    ms, units = float(ms_local), float(units_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        u = torch.tensor([units], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, units = float(t.item()), float(u.item())
+    return ms, units / (ms * 1e-3)
+
+
 def run_vjp(gks, I, S, Q0, dt, torch, stream, calls=3):
     """ms per residual VJP (gks_residual_vjp: FP64 reconstruction recomputed, then the reverse
     passes of the flux, polynomial evaluation, reconstruction and stencil gathers)."""
@@ -312,12 +326,8 @@ def run_gpu(args):
     mixed = measure(gks.GKS_PREC_MIXED, args.steps, args.warmup)
     S = mixed["solver"]
     nc, nf = S.n_cells, S.n_faces
-    ms_total = mixed["ms"]
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * nc * 2 * args.steps / (ms_total * 1e-3)
+    ms_total, value = job_rate(mixed["ms"], nc * 2 * args.steps, world,
+                               dist if world > 1 else None)
 
     # FP64 path on the same inputs and dt
     fp64_steps = args.fp64_steps or max(3, args.steps // 4)
