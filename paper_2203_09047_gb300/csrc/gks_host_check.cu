@@ -29,7 +29,7 @@ gks::WallData<double> wall_from(const double* p, int code) {
     const int w = code % 6;
     for (int a = 0; a < 3; ++a) d.uw[a] = p[9 + 3 * w + a];
     d.Tw = p[27 + w];
-    for (int v = 0; v < 5; ++v) d.finf[v] = p[33 + 5 * w + v];
+    d.finf = p + 33 + 5 * w;  // the caller's vector holds the plane's far-field state
   }
   return d;
 }

@@ -417,7 +417,7 @@ template <class R>
 struct WallData {
   R uw[3] = {R(0), R(0), R(0)};
   R Tw = R(0);
-  R finf[5] = {R(1), R(0), R(0), R(0), R(1)};
+  const R* finf = nullptr;  // far-field planes: (rho, U, V, W, p) in the table
 };
 template <class R>
 GKS_HD WallData<R> wall_data(const R* table, int code) {
@@ -427,10 +427,7 @@ GKS_HD WallData<R> wall_data(const R* table, int code) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) d.uw[a] = t[a];
     d.Tw = t[3];
-    if (code >= 12) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) d.finf[v] = t[4 + v];
-    }
+    d.finf = t + 4;
   }
   return d;
 }
