@@ -133,7 +133,12 @@ const char* gks_mesh_last_error(void);
  * least-squares pseudo-inverses of every big stencil and sub-stencil, and stores them in the
  * precision of p->precision. `stream` is a cudaStream_t (NULL: the legacy default stream) on
  * which every later call enqueues its work. The mesh may be destroyed afterwards.
- * Errors: GKS_E_INVAL (params), GKS_E_MESH (inverted cell), GKS_E_SINGULAR (rank-deficient
+ * With moving no-slip walls or far-field planes it also sets up the ghost cells of the stencil
+ * images whose flow variables are not a sign change of their source cell (refreshed before
+ * every reconstruction).
+ * Errors: GKS_E_INVAL (params: gamma, mu, Pr, the modes, the WENO constants, T_ref > 0 for the
+ * power law, finite wall data, far-field states with rho > 0 and p > 0), GKS_E_MESH (inverted
+ * cell; too many ghost cells for the stencil entry format), GKS_E_SINGULAR (rank-deficient
  * stencil), GKS_E_NOMEM, GKS_E_CUDA. */
 gks_status gks_init(const gks_mesh* m, const gks_params* p, void* stream, gks_solver** out);
 
