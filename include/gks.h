@@ -58,8 +58,11 @@ enum { GKS_FLUX_SMOOTH = 0, GKS_FLUX_FULL = 1 };
  * power law of Section 5.4, mu(T) = mu (T/T_ref)^mu_pow with T = p/rho of the interface
  * equilibrium. */
 enum { GKS_TAU_ZERO = 0, GKS_TAU_INVISCID = 1, GKS_TAU_VISCOUS = 2, GKS_TAU_POWER_LAW = 3 };
-/* Arithmetic: FP64 everywhere, or FP32 reconstruction and flux with FP64 stencil
- * differences, FP64 face sums and FP64 update. */
+/* Arithmetic: FP64 everywhere, or FP32 reconstruction and flux with the state, the stencil
+ * differences, the face sums and the two-stage update in float-float arithmetic (each value an
+ * unevaluated sum of two FP32 numbers, about 48 significant bits; error-free TwoSum and FMA
+ * TwoProduct), which conserves mass, momentum and energy to about 2^-46 relative per update
+ * and executes no FP64 instruction on the hot path. */
 enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
 
 typedef struct {
@@ -205,25 +208,29 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
 gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
                             const double* gLt, double* gQ);
 
-/* Per-kernel timing for benchmarks and traces. With enable != 0 every later hot-path launch is
+/* Per-kernel timing for benchmarks and traces (a utility of this library; the paper has no
+ * counterpart). With enable != 0 every later hot-path launch is
  * bracketed by CUDA events on the solver's stream. gks_timing_read synchronises the stream and
  * returns, for the kinds 0 reconstruction, 1 face flux, 2 face sum + update, the summed device
  * milliseconds and the number of launches since the last read, then resets them. */
 gks_status gks_timing_enable(gks_solver* s, int enable);
 gks_status gks_timing_read(gks_solver* s, double ms[3], int64_t counts[3]);
 
-/* Algorithmic bytes of one pass of each hot kernel over the mesh (0 reconstruction, 1 face flux,
+/* Algorithmic bytes (a utility of this library; the paper has no counterpart) of one pass of
+ * each hot kernel over the mesh (0 reconstruction, 1 face flux,
  * 2 face sum + update as in a two-stage step) for this solver's mesh and precision: every array
  * the kernel must read or write counted once (re-reads through the caches are not counted). */
 gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]);
 
-/* Kernel launches in one pass of each hot kernel (0 reconstruction: one launch per range of
+/* Kernel launches (a utility of this library; the paper has no counterpart) in one pass of
+ * each hot kernel (0 reconstruction: one launch per range of
  * tiles of one cell kind, plus the ghost refresh when moving no-slip walls need ghost cells;
  * 1 face flux; 2 face sum + update), for counting the launches of a timed region from the pass
  * counts of gks_timing_read. */
 gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]);
 
-/* Algorithmic operation count of one face Gauss point of the flux kernel for a flux mode and
+/* Algorithmic operation count (a utility of this library; the paper has no counterpart) of one
+ * face Gauss point of the flux kernel for a flux mode and
  * collision-time model: *flops counts +, -, *, / (an FMA as two), *special counts exp, erfc and
  * sqrt. Computed on the host by running the kernel's own templated arithmetic with a counting
  * scalar type. Returns 0 on success. Not thread-safe. */
@@ -233,7 +240,9 @@ int gks_flux_opcount(int flux_mode, int tau_model, double* flops, double* specia
  * whose device memory is owned by another allocator (a framework pool that has reserved the
  * device) or latency-critical loops that must not pay for cudaMalloc's implicit device
  * synchronisation. The paper has no counterpart; it is the time-step reduction of gks_max_dt
- * written as a stand-alone call whose scratch is a fixed array inside the library.
+ * written as a stand-alone call whose scratch is a fixed array inside the library. Its viscosity
+ * mu is one constant, so it equals gks_max_dt for the collision-time models with constant
+ * viscosity and not for GKS_TAU_POWER_LAW, whose bound uses mu(T) of each cell.
  *   n_cells  number of cells, at most 16,777,216 (65,536 blocks of 256 cells: the scratch holds
  *            one 8-byte partial minimum per block, 512 KiB per device); larger n is rejected with
  *            GKS_E_INVAL and a message in gks_last_error(NULL).
@@ -241,13 +250,16 @@ int gks_flux_opcount(int flux_mode, int tau_model, double* flops, double* specia
  *   h        device pointer, float64 [n_cells] length of each cell in the same order (the solver
  *            uses |Omega_i| / largest face area).
  *   dt       device pointer to one float64: receives cfl * min_i h_i / (|U_i| + c_i +
- *            2 mu / (rho_i h_i)), or -1 if any cell has rho <= 0, p <= 0 or NaN.
+ *            2 mu / (rho_i h_i)), or -1 if any cell has rho <= 0, p <= 0 or NaN (each tested on the
+ *            primitive itself, before the bound is formed).
  *   stream   cudaStream_t on which both kernels are enqueued; the call does not synchronise.
  * It calls no cudaMalloc, cudaFree or allocating library routine. The first call on a device
  * looks up the device address of the scratch array (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture. Every call on a device shares the
  * one scratch array, so calls whose kernels overlap on the GPU (different streams, no ordering)
- * race on it; order them on one stream. Returns GKS_OK once both kernels are enqueued. */
+ * race on it; order them on one stream. The looked-up address is kept per device ordinal for
+ * the life of the process: the call assumes the runtime's primary context of that device and no
+ * cudaDeviceReset between calls. Returns GKS_OK once both kernels are enqueued. */
 gks_status gks_cfl_dt_noalloc(int64_t n_cells, const double* Q, const double* h, double gamma,
                               double mu, double cfl, double* dt, void* stream);
 

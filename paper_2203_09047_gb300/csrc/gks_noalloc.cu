@@ -39,10 +39,17 @@ __global__ void __launch_bounds__(kThreads) k_cfl_partial(int64_t n, const doubl
     const double r = Q[i], mx = Q[n + i], my = Q[2 * n + i], mz = Q[3 * n + i], E = Q[4 * n + i];
     const double u2 = (mx * mx + my * my + mz * mz) / (r * r);
     const double p = (gamma - 1.0) * (E - 0.5 * r * u2);
-    const double c = sqrt(gamma * p / r);
-    const double hi = h[i];
-    best = hi / (sqrt(u2) + c + 2.0 * mu / (r * hi));
-    if (!(best >= 0.0)) best = -1.0;  // non-physical state (NaN or negative pressure)
+    // The primitives are tested themselves: rho < 0 with p < 0 gives a positive gamma p / rho,
+    // and p = 0 a zero sound speed, so a test of the bound alone would miss both. The negated
+    // comparisons also catch NaN.
+    if (!(r > 0.0) || !(p > 0.0)) {
+      best = -1.0;
+    } else {
+      const double c = sqrt(gamma * p / r);
+      const double hi = h[i];
+      best = hi / (sqrt(u2) + c + 2.0 * mu / (r * hi));
+      if (!(best >= 0.0)) best = -1.0;  // NaN in the velocity or the cell length
+    }
   }
   for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;

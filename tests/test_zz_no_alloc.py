@@ -67,9 +67,24 @@ def test_noalloc_dt_matches_max_dt_twice(setup):
 
 def test_noalloc_dt_flags_nonphysical_and_rejects_oversize(setup):
     m, om, h = setup
-    Q = om.advection_average()
+    Q0 = om.advection_average()
+    Q = Q0.copy()
     Q[4, 5] = 0.0  # negative pressure in one cell
     assert _noalloc(Q, h, 1.4, 0.0, 0.5) == -1.0
+    # zero pressure: the sound speed is 0 and the bound alone would stay positive
+    Q = Q0.copy()
+    Q[4, 7] = 0.5 * (Q[1, 7] ** 2 + Q[2, 7] ** 2 + Q[3, 7] ** 2) / Q[0, 7]
+    assert _noalloc(Q, h, 1.4, 0.0, 0.5) == -1.0
+    # negative density and negative pressure: gamma p / rho is positive, c is real
+    Q = Q0.copy()
+    Q[:, 9] = [-1.0, 0.0, 0.0, 0.0, -1.0]
+    assert _noalloc(Q, h, 1.4, 0.0, 0.5) == -1.0
+    # a NaN anywhere in a cell
+    Q = Q0.copy()
+    Q[2, 11] = float("nan")
+    assert _noalloc(Q, h, 1.4, 0.0, 0.5) == -1.0
+    # the physical state itself stays positive after those calls reused the scratch
+    assert _noalloc(Q0, h, 1.4, 0.0, 0.5) > 0.0
     tiny = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(gks.GksError) as e:
         # rejected on the host before any launch
