@@ -80,6 +80,9 @@ def lib():
         L.oracle_cell_average.argtypes = [P, ctypes.c_int, ctypes.c_double, D, D]
         L.oracle_reconstruct_at.argtypes = [P, D, D, ctypes.c_int, I, D, D]
         L.oracle_gp_flux.argtypes = [D, D, D, D, D, ctypes.c_double, D]
+        L.oracle_weno_detail.argtypes = [P, D, D, ctypes.c_int, D, D, D, D, D, I, D]
+        L.oracle_weno_weights.restype = ctypes.c_double
+        L.oracle_weno_weights.argtypes = [D, ctypes.c_int, D, D]
         L.oracle_time_coeffs.argtypes = [ctypes.c_double, ctypes.c_double, D]
         L.oracle_wall_ghost.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D, D]
         L.oracle_slope.argtypes = [ctypes.c_double] * 5 + [D, D]
@@ -175,6 +178,23 @@ class Mesh:
         lib().oracle_reconstruct_at(self.h, _d(params), _d(Q), len(cells), _i(cells), _d(x), _d(out))
         return out
 
+    def weno_detail(self, params, Q, cell):
+        """The parts of one cell's WENO reconstruction (Section 2), per conserved variable:
+        a [5][9] (P0 in the basis x, y, z, xx, yy, zz, xy, xz, yz of coordinates about the
+        centroid scaled by h = |Omega|^(1/3)), b [5][M][3], beta [5][M+1], wbar [5][M+1],
+        tau [5], and h."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        a, b = np.zeros((5, 9)), np.zeros((5, 16, 3))
+        beta, wbar, tau = np.zeros((5, 17)), np.zeros((5, 17)), np.zeros(5)
+        M, h = ctypes.c_int(0), np.zeros(1)
+        st = lib().oracle_weno_detail(self.h, _d(params), _d(Q), int(cell), _d(a), _d(b), _d(beta),
+                                      _d(wbar), _d(tau), ctypes.byref(M), _d(h))
+        if st:
+            raise OracleError(st)
+        M = M.value
+        return dict(a=a, b=b[:, :M], beta=beta[:, :M + 1], wbar=wbar[:, :M + 1], tau=tau, M=M,
+                    h=float(h[0]))
+
     def residual(self, params, Q, dt):
         Q = np.ascontiguousarray(Q, dtype=np.float64)
         L, Lt = np.zeros_like(Q), np.zeros_like(Q)
@@ -243,6 +263,14 @@ def gp_flux(params, ql, dql, qr, dqr, dt):
     if st:
         raise OracleError(st)
     return F
+
+
+def weno_weights(params, beta):
+    """Normalised nonlinear weights wbar[0..M] and tau from indicators beta[0..M] (Section 2)."""
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    wbar = np.zeros_like(beta)
+    tau = lib().oracle_weno_weights(_d(params), len(beta) - 1, _d(beta), _d(wbar))
+    return wbar, float(tau)
 
 
 def wall_ghost(params, kind, plane, v, g):

@@ -743,6 +743,8 @@ struct Recon {
   T a[5][9];                      // P0 coefficients per variable
   std::vector<std::array<T, 3>> b[5];  // P_m coefficients per variable
   T wbar[5][17];                  // normalised weights omega-bar_0..M
+  T beta[5][17];                  // smoothness indicators beta_0..M (Eq. indicator)
+  T tau[5];                       // tau of the nonlinear weights
   double g0;                      // gamma_0
   double gm;                      // gamma_m
   int M;
@@ -776,6 +778,27 @@ void transform_state(const Mesh& m, const Params& P, const Xform& X, const T* q,
     out[4] = out[4] + 2.0 * uw2 * out[0] - 2.0 * um;
     for (int a = 0; a < 3; ++a) out[1 + a] = 2.0 * uw[a] * out[0] - out[1 + a];
   }
+}
+
+// Nonlinear weights of Section 2 from the indicators beta[0..M] of P0 and the M linear
+// candidates: tau = sum_m |beta_0 - beta_m| / M, omega_m = gamma_m (1 + (tau / (beta_m + eps))^q)
+// with gamma_m = weno_gamma for m >= 1, gamma_0 = 1 - M weno_gamma and q = weno_pow (printed: 1),
+// then wbar_m = omega_m / sum_k omega_k. Returns tau.
+template <class T>
+T nonlinear_weights(const Params& P, int M, const T* beta, T* wbar) {
+  T tau = T(0.0);
+  for (int s = 1; s <= M; ++s) tau += fabs(beta[0] - beta[s]) / double(M);
+  T sum = T(0.0);
+  for (int s = 0; s <= M; ++s) {
+    const double gam = s == 0 ? 1.0 - P.weno_gamma * M : P.weno_gamma;
+    const T ratio = tau / (beta[s] + P.weno_eps);
+    T pw = ratio;
+    for (int e = 1; e < P.weno_pow; ++e) pw = pw * ratio;
+    wbar[s] = gam * (1.0 + pw);
+    sum += wbar[s];
+  }
+  for (int s = 0; s <= M; ++s) wbar[s] = wbar[s] / sum;
+  return tau;
 }
 
 template <class T>
@@ -832,21 +855,11 @@ void reconstruct_cell(const Mesh& m, const Params& P, const T* Q, int n, int i, 
           betam[s] += std::pow(vol, -1.0 / 3.0) * q.w[g] * d * d;
         }
     }
-    // nonlinear weights
-    T tau = T(0.0);
-    for (int s = 0; s < M; ++s) tau += fabs(beta0 - betam[s]) / double(M);
-    std::vector<T> w(M + 1);
-    auto weight = [&](double gam, T beta) {
-      T ratio = tau / (beta + P.weno_eps);
-      T p = ratio;
-      for (int e = 1; e < P.weno_pow; ++e) p = p * ratio;
-      return gam * (1.0 + p);
-    };
-    w[0] = weight(r.g0, beta0);
-    for (int s = 0; s < M; ++s) w[s + 1] = weight(r.gm, betam[s]);
-    T sum = T(0.0);
-    for (int s = 0; s <= M; ++s) sum += w[s];
-    for (int s = 0; s <= M; ++s) r.wbar[v][s] = P.weno_linear ? T(s == 0 ? r.g0 : r.gm) : w[s] / sum;
+    r.beta[v][0] = beta0;
+    for (int s = 0; s < M; ++s) r.beta[v][s + 1] = betam[s];
+    r.tau[v] = nonlinear_weights(P, M, r.beta[v], r.wbar[v]);
+    if (P.weno_linear)
+      for (int s = 0; s <= M; ++s) r.wbar[v][s] = T(s == 0 ? r.g0 : r.gm);
   }
 }
 
@@ -1737,6 +1750,40 @@ int oracle_reconstruct_at(void* h, const double* params, const double* Q, int np
     }
   }
   return ST_OK;
+}
+
+// The parts of one cell's reconstruction (Section 2), per conserved variable v: a[v][9] the
+// coefficients of P0 in the scaled basis (x, y, z, xx, yy, zz, xy, xz, yz about the centroid,
+// divided by h = |Omega|^(1/3) per power), b[v][M][3] those of the linear candidates, beta[v][M+1]
+// and wbar[v][M+1] the indicators and normalised weights, tau[v]. Arrays are sized for M <= 16;
+// *M_out and *h_out return M and h.
+int oracle_weno_detail(void* h, const double* params, const double* Q, int cell, double* a,
+                       double* b, double* beta, double* wbar, double* tau, int* M_out,
+                       double* h_out) {
+  Mesh* m = static_cast<Mesh*>(h);
+  const Params P = read_params(params);
+  if (cell < 0 || cell >= m->n_cells) return ST_INVAL;
+  Recon<double> r;
+  reconstruct_cell(*m, P, Q, m->n_cells, cell, r);
+  *M_out = r.M;
+  *h_out = m->cells[cell].h;
+  for (int v = 0; v < 5; ++v) {
+    for (int k = 0; k < 9; ++k) a[9 * v + k] = r.a[v][k];
+    for (int s = 0; s < r.M; ++s)
+      for (int k = 0; k < 3; ++k) b[(v * 16 + s) * 3 + k] = r.b[v][s][k];
+    for (int s = 0; s <= r.M; ++s) {
+      beta[17 * v + s] = r.beta[v][s];
+      wbar[17 * v + s] = r.wbar[v][s];
+    }
+    tau[v] = r.tau[v];
+  }
+  return ST_OK;
+}
+
+// The nonlinear weights alone, from given indicators beta[0..M]: wbar[0..M]; returns tau.
+double oracle_weno_weights(const double* params, int M, const double* beta, double* wbar) {
+  const Params P = read_params(params);
+  return nonlinear_weights(P, M, beta, wbar);
 }
 
 // One Gauss-point flux in the local frame: F[2][5] = time integrals over [0, dt/2], [0, dt].
