@@ -98,11 +98,19 @@ typedef struct {
    * per plane (axis + 3 side), default (1, 0, 0, 0, 1/1.4). gks_residual_vjp rejects meshes
    * with far-field planes (GKS_E_INVAL). */
   double farfield[6][5];
+  /* Positivity fallback at the Gauss points (not in the paper, which prints no positivity
+   * treatment; off by default): with gp_fallback != 0, a side whose reconstructed state at a face
+   * Gauss point has rho <= 0 or p <= 0 (or NaN) takes its cell average with a zero gradient,
+   * the first-order state, before any wall ghost is formed from it. The face flux stays one
+   * value per face, so conservation is kept. Off: such a state stops the step with
+   * GKS_E_NONPHYSICAL (the paper's method as printed). gks_residual_vjp differentiates the
+   * fallback: the cotangent of a side that fell back goes to its cell average. */
+  int gp_fallback;
 } gks_params;
 
 /* Fill *p with the defaults above (gamma 1.4, Euler, smooth flux, zero collision time,
  * weno_gamma 0.0125, weno_eps 1e-8, weno_pow 1, FP64, T_ref 1, mu_pow 0.7, stationary
- * adiabatic walls, far field at rest with rho 1 and p 1/1.4). */
+ * adiabatic walls, far field at rest with rho 1 and p 1/1.4, no Gauss-point fallback). */
 void gks_params_default(gks_params* p);
 
 /* Build the mesh topology on the host.

@@ -19,7 +19,7 @@ _lib = None
 # Parameter vector layout: gamma, mu, Pr, flux_mode, tau_model, tau_eps, tau_C, weno_gamma,
 # weno_eps, weno_pow, weno_linear, T_ref, mu_pow, then per wall plane (axis + 3 side, side 1 the
 # upper plane) the wall velocity (3) and temperature (<= 0: adiabatic), then per plane the
-# far-field state (rho, U, V, W, p).
+# far-field state (rho, U, V, W, p), then the Gauss-point positivity fallback switch.
 DEFAULTS = dict(gamma=1.4, mu=0.0, Pr=1.0, flux_mode=0, tau_model=0, tau_eps=0.01, tau_C=1.0,
                 weno_gamma=0.0125, weno_eps=1e-8, weno_pow=1, weno_linear=0, T_ref=1.0,
                 mu_pow=0.7)
@@ -27,7 +27,7 @@ _ORDER = ["gamma", "mu", "Pr", "flux_mode", "tau_model", "tau_eps", "tau_C", "we
           "weno_eps", "weno_pow", "weno_linear", "T_ref", "mu_pow"]
 
 
-def params_vec(wall_u=None, wall_T=None, farfield=None, **kw) -> np.ndarray:
+def params_vec(wall_u=None, wall_T=None, farfield=None, gp_fallback=0, **kw) -> np.ndarray:
     """wall_u [6][3] and wall_T [6]: velocity and temperature of each wall plane (axis + 3 side);
     zero velocity and adiabatic walls by default. farfield: (rho, U, V, W, p) of the far field,
     one for all planes or [6][5] per plane (default 1, 0, 0, 0, 1/1.4)."""
@@ -45,7 +45,7 @@ def params_vec(wall_u=None, wall_T=None, farfield=None, **kw) -> np.ndarray:
         np.asarray(farfield, dtype=np.float64)
     ff = np.broadcast_to(ff, (6, 5)).ravel() if ff.size == 5 else ff.reshape(30)
     return np.concatenate([np.array([float(d[k]) for k in _ORDER], dtype=np.float64),
-                           walls.ravel(), ff])
+                           walls.ravel(), ff, [float(gp_fallback)]])
 
 
 def build(force: bool = False) -> str:

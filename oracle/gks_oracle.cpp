@@ -331,6 +331,8 @@ struct Params {
   double T_ref, mu_pow;   // mu(T) = mu (T / T_ref)^mu_pow, T = p / rho (Section 5.4)
   double uw[6][3], Tw[6];  // per wall plane (axis + 3 side): velocity, temperature (<= 0: adiabatic)
   double finf[6][5];       // far-field state per plane: rho, U, V, W, p
+  int gp_fallback;  // 1: a side whose reconstructed state at a Gauss point has rho <= 0 or
+                    // p <= 0 takes its cell average with zero gradient (not in the paper)
 };
 Params read_params(const double* p) {
   Params q;
@@ -353,6 +355,7 @@ Params read_params(const double* p) {
   }
   for (int w = 0; w < 6; ++w)
     for (int v = 0; v < 5; ++v) q.finf[w][v] = p[37 + 5 * w + v];
+  q.gp_fallback = (int)p[67];
   return q;
 }
 
@@ -1352,6 +1355,25 @@ void wall_ghost(const Params& P, int kind, int plane, const T* v, const T g[5][3
     }
 }
 
+// Positivity fallback at one Gauss point (a reading, not in the paper, which prints no
+// positivity treatment): when the reconstructed state of a side has rho <= 0 or p <= 0 (or is
+// NaN), that side takes its cell average and a zero gradient, the first-order state.
+template <class T>
+bool physical_state(const T q[5]) {
+  // p > 0 written as rho E > |m|^2 / 2 (rho > 0): the form the decision takes on both sides
+  const double r = val(q[0]);
+  const double m2 = val(q[1]) * val(q[1]) + val(q[2]) * val(q[2]) + val(q[3]) * val(q[3]);
+  return r > 0.0 && r * val(q[4]) > 0.5 * m2;
+}
+template <class T>
+void gp_first_order(const Recon<T>& r, T v[5], T g[5][3]) {
+  if (physical_state(v)) return;
+  for (int c = 0; c < 5; ++c) {
+    v[c] = r.Q0[c];
+    for (int a = 0; a < 3; ++a) g[c][a] = T(0.0);
+  }
+}
+
 // Face flux (Eq. flux-qud over the 2x2 Gauss points) fitted in time:
 // out[0..4] = F^n, out[5..9] = dF/dt. Returns false for a non-physical state.
 template <class T>
@@ -1364,11 +1386,13 @@ bool face_flux(const Mesh& m, const Params& P, const Face& fc, const Recon<T>& r
     for (int k = 0; k < 4; ++k) {
       T vl[5], gl[5][3], vr[5], gr[5][3];
       eval_recon(m, fc.owner, ro, fc.xg[k], vl, gl);
+      if (P.gp_fallback) gp_first_order(ro, vl, gl);
       if (fc.nb >= 0) {
         double xn[3];
         for (int a = 0; a < 3; ++a) xn[a] = (fc.xg[k][a] - fc.nb_to_owner.t[a]) / fc.nb_to_owner.s[a];
         T v0[5], g0[5][3];
         eval_recon(m, fc.nb, *rn, xn, v0, g0);
+        if (P.gp_fallback) gp_first_order(*rn, v0, g0);
         transform_state(m, P, fc.nb_to_owner, v0, vr);
         for (int v = 0; v < 5; ++v) {
           const double sv = (v >= 1 && v <= 3 && ((fc.nb_to_owner.vflip >> (v - 1)) & 1)) ? -1.0 : 1.0;

@@ -35,7 +35,7 @@ class gks_params(ctypes.Structure):
                 ("weno_pow", ctypes.c_int), ("precision", ctypes.c_int),
                 ("T_ref", ctypes.c_double), ("mu_pow", ctypes.c_double),
                 ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6),
-                ("farfield", (ctypes.c_double * 5) * 6)]
+                ("farfield", (ctypes.c_double * 5) * 6), ("gp_fallback", ctypes.c_int)]
 
 
 class GksError(RuntimeError):
@@ -353,6 +353,10 @@ class Solver:
         gks_step(self.h, dt, nsteps)
         if check:
             gks_check(self.h)
+
+    def check(self):
+        """Raise GksError if an earlier step met a non-physical state (gks_check)."""
+        gks_check(self.h)
 
     def step_implicit(self, dt: float, nsteps: int = 1, kmax: int = 3, check: bool = True):
         """Implicit backward-Euler steps with kmax Jacobi iterations (Section 4)."""

@@ -24,6 +24,44 @@ struct PolyRef64 {
   __device__ __forceinline__ double operator()(int v, int j) const { return p[10 * v + j]; }
 };
 
+// Positivity fallback (the forward flux's, mirrored): a side whose reconstructed Gauss-point
+// state has rho <= 0 or p <= 0 takes its cell average with a zero gradient. Here the cell average
+// is written as the mean of the cell's own polynomial, c0 + sum_j c_j <d_j> over the quadratic
+// terms (<d_j> the cell's central second moments: scaled moments times h^2), which equals the
+// cell average for every state, so that its cotangent flows back through the reconstruction.
+__device__ __forceinline__ bool nonphysical(const double v[5]) {
+  const double m2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  return !(v[0] > 0.0 && v[0] * v[4] > 0.5 * m2);
+}
+__device__ __forceinline__ void central_moments(const double* __restrict__ mom,
+                                                const double* __restrict__ hcell, int64_t nc,
+                                                int64_t c, double mu[6]) {
+  const double h2 = hcell[c] * hcell[c];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) mu[q] = mom[q * nc + c] * h2;
+}
+__device__ __forceinline__ void poly_mean(const double* __restrict__ p, const double mu[6],
+                                          double v[5], double g[5][3]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double s = p[10 * k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) s += p[10 * k + 4 + q] * mu[q];
+    v[k] = s;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[k][a] = 0.0;
+  }
+}
+__device__ __forceinline__ void poly_mean_adj(const double mu[6], const double gv[5],
+                                              double gp[5][10]) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    gp[k][0] += gv[k];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) gp[k][4 + q] += gv[k] * mu[q];
+  }
+}
+
 // kFull and kTau0 fix the flux form and a zero collision time at compile time (as in the forward
 // kernel), so that each instance holds only its own form's recomputed forward state. kWalls =
 // false is the instance for meshes without boundary planes (every face has two cells; no
@@ -34,7 +72,8 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
     const int8_t* __restrict__ f_wall, const double* __restrict__ fgp,
     const double* __restrict__ poly, const double* __restrict__ gL, const double* __restrict__ gLt,
     const double* __restrict__ vol, int64_t nc, FluxParams<double> P,
-    const double* __restrict__ wall_tab, double dt, double* __restrict__ gpf, int* flag) {
+    const double* __restrict__ wall_tab, double dt, int fallback, const double* __restrict__ mom,
+    const double* __restrict__ hcell, double* __restrict__ gpf, int* flag) {
   P.full = kFull;
   if (kTau0) P.tau_model = 0;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -77,8 +116,21 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
     const double w = fgp[9 * stride + gid];
     double vl[5], gl[5][3], vr[5], gr[5][3];
     eval_poly(PolyRef64{poly + (int64_t)kPolyStride * o}, dl, vl, gl);
+    const bool fbl = fallback && nonphysical(vl);
+    double mu[6];
+    if (fbl) {
+      central_moments(mom, hcell, nc, o, mu);
+      poly_mean(poly + (int64_t)kPolyStride * o, mu, vl, gl);
+    }
+    bool fbr = false;
     if (!kWalls || nb >= 0) {
       eval_poly(PolyRef64{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
+      fbr = fallback && nonphysical(vr);
+      if (fbr) {
+        double mun[6];
+        central_moments(mom, hcell, nc, nb, mun);
+        poly_mean(poly + (int64_t)kPolyStride * nb, mun, vr, gr);
+      }
     } else {
       wall_ghost<double, false>(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
     }
@@ -92,8 +144,17 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
       // the wall's ghost is a function of the owner's value and gradient: fold its cotangent back
       if (kWalls && nb < 0)
         wall_ghost_vjp(P, wall, wall_data(wall_tab, wall), vl, gl, gvr, ggr, gvl, ggl);
-      eval_poly_adj(dl, gvl, ggl, go);
-      if (!kWalls || nb >= 0) eval_poly_adj(dr, gvr, ggr, gn);
+      if (fbl)
+        poly_mean_adj(mu, gvl, go);
+      else
+        eval_poly_adj(dl, gvl, ggl, go);
+      if (fbr) {
+        double mun[6];
+        central_moments(mom, hcell, nc, nb, mun);
+        poly_mean_adj(mun, gvr, gn);
+      } else if (!kWalls || nb >= 0) {
+        eval_poly_adj(dr, gvr, ggr, gn);
+      }
     } else {
       atomicOr(flag, kErrNonphysical);
     }
@@ -438,8 +499,8 @@ void launch_vjp(const DevMesh& m, const Geo64& g64, const GeoR<double>& g, const
       cudaDeviceGetLimit(&cur, cudaLimitStackSize) == cudaSuccess && at.localSizeBytes > cur)
     cudaDeviceSetLimit(cudaLimitStackSize, at.localSizeBytes);
   kern<<<blocks_for(4 * m.nf, 128), 128, 0, st>>>(m.nf, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly,
-                                                  gL, gLt, g64.vol, m.nc, fp, m.wall64, dt, gpf,
-                                                  flag);
+                                                  gL, gLt, g64.vol, m.nc, fp, m.wall64, dt,
+                                                  p.gp_fallback, g.mom, g.h, gpf, flag);
   k_vjp_poly<<<blocks_for(m.nc, 128), 128, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, gpf, gpc);
   k_vjp_recon<<<blocks_for(m.nc, 64), 64, 0, st>>>(m.nc, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
                                                      m.t_idx, m.st_ptr, m.n_sub, g.Ap, g.Bp, g.mom,

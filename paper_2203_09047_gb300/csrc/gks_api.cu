@@ -153,6 +153,7 @@ KParams<R> kparams(const gks_params& p) {
   k.weno_pow = p.weno_pow;
   k.T_ref = (R)p.T_ref;
   k.mu_pow = (R)p.mu_pow;
+  k.gp_fallback = p.gp_fallback != 0;
   return k;
 }
 
@@ -208,7 +209,8 @@ void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode
   launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st, &s->fj);
   s->tock(t);
   t = s->tick(1);
-  launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
+  launch_flux<R>(s->m, g, kp, (const R*)s->poly, (const R*)QinA, dt, (R*)s->fface, s->flag,
+                 s->st);
   s->tock(t);
   t = s->tick(2);
   if (mode == 0)
@@ -433,7 +435,8 @@ gks_status step_implicit_r(gks_solver* s, GeoR<R>& g, double dt, int nsteps, int
     launch_recon<R>(s->m, g, kp, (const R*)s->QA, (R*)s->poly, s->flag, s->st, &s->fj);
     s->tock(t);
     t = s->tick(1);
-    launch_flux<R>(s->m, g, kp, (const R*)s->poly, dt, (R*)s->fface, s->flag, s->st);
+    launch_flux<R>(s->m, g, kp, (const R*)s->poly, (const R*)s->QA, dt, (R*)s->fface, s->flag,
+                   s->st);
     s->tock(t);
     t = s->tick(2);
     launch_jacobi_init<R>(s->m, (const R*)s->fface, (const R*)s->jfn, s->g.vol, dt,
@@ -479,6 +482,7 @@ void gks_params_default(gks_params* p) {
     p->farfield[w][1] = p->farfield[w][2] = p->farfield[w][3] = 0.0;
     p->farfield[w][4] = 1.0 / 1.4;
   }
+  p->gp_fallback = 0;
 }
 
 gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,

@@ -138,6 +138,7 @@ struct KParams {
   R weno_gamma, weno_eps;
   int weno_pow;
   R T_ref, mu_pow;  // power-law viscosity (the boundary planes live in DevMesh::wall64/wall32)
+  int gp_fallback;  // first-order state at Gauss points whose reconstruction is non-physical
 };
 
 // ---- precompute (gks_geom.cu) -------------------------------------------------------------
@@ -170,7 +171,7 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
                   R* poly, int* flag, cudaStream_t st, const ForkJoin* fj = nullptr);
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
-                 double dt, R* fface, int* flag, cudaStream_t st);
+                 const R* QA, double dt, R* fface, int* flag, cudaStream_t st);
 // Residual output: L = -(1/|Omega|) sum_f s_f F_f and Lt likewise from dF/dt, in FP64.
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,

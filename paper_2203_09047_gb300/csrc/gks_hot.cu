@@ -434,6 +434,25 @@ __device__ __forceinline__ void load_coefs(const PolyRef<double>& c, int v, doub
   }
 }
 
+// Positivity fallback at a Gauss point (off unless the solver asks for it; the paper prints no
+// positivity treatment): a side whose reconstructed state has rho <= 0 or p <= 0 (or NaN) takes
+// the cell average of its cell, read from the gather copy the reconstruction used, with a zero
+// gradient. p > 0 is tested as rho E > |m|^2 / 2, which needs no division.
+template <class R>
+__device__ __forceinline__ void first_order_if_nonphysical(const R* __restrict__ QA, int64_t c,
+                                                           R v[5], R g[5][3]) {
+  const R m2 = v[1] * v[1] + v[2] * v[2] + v[3] * v[3];
+  if (v[0] > R(0) && v[0] * v[4] > R(0.5) * m2) return;
+  Gq<R> q;
+  q.load(QA, c);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    v[k] = q.value(k);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[k][a] = R(0);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Flux: four consecutive threads per face, one per Gauss point. Each evaluates both sides'
 // reconstructions, rotates into the local frame (n1 normal, n2 = n1 x e_k normalised with e_k
@@ -453,7 +472,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
     const int8_t* __restrict__ f_wall, const R* __restrict__ fgp, const R* __restrict__ poly,
-    FluxParams<R> P, const R* __restrict__ wall_tab, R dt, R* __restrict__ fface, int* flag) {
+    const R* __restrict__ QA, int fallback, FluxParams<R> P, const R* __restrict__ wall_tab, R dt,
+    R* __restrict__ fface, int* flag) {
   P.full = kFull;
   if (kTau0) P.tau_model = 0;
   const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -477,8 +497,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     const R w = __ldcs(fgp + 9 * stride + gid);
     R vl[5], gl[5][3], vr[5], gr[5][3];
     eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * o}, dl, vl, gl);
+    if (fallback) first_order_if_nonphysical(QA, o, vl, gl);
     if (nb >= 0) {
       eval_poly(PolyRef<R>{poly + (int64_t)kPolyStride * nb}, dr, vr, gr);
+      if (fallback) first_order_if_nonphysical(QA, nb, vr, gr);
     } else {
       wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);  // the wall's ghost
     }
@@ -1114,13 +1136,13 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
 }
 template <class R>
 void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* poly,
-                 double dt, R* fface, int* flag, cudaStream_t st) {
+                 const R* QA, double dt, R* fface, int* flag, cudaStream_t st) {
   const FluxParams<R> fp = flux_params(p);
   const unsigned nb = blocks_for(4 * m.nf, 128);
   auto kern = fp.full ? (fp.tau_model == 0 ? k_flux<R, true, true> : k_flux<R, true, false>)
                       : (fp.tau_model == 0 ? k_flux<R, false, true> : k_flux<R, false, false>);
-  kern<<<nb, 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly, fp,
-                           wall_table<R>(m), (R)dt, fface, flag);
+  kern<<<nb, 128, 0, st>>>(m.nf, m.nc, m.f_owner, m.f_nb, m.f_wall, g.fgp, poly, QA,
+                           p.gp_fallback, fp, wall_table<R>(m), (R)dt, fface, flag);
 }
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,
@@ -1216,9 +1238,10 @@ template void launch_permute_in<float>(int64_t, const int32_t*, const double*, d
 template void launch_recon<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
                                   const float*, float*, int*, cudaStream_t, const ForkJoin*);
 template void launch_flux<double>(const DevMesh&, const GeoR<double>&, const KParams<double>&,
-                                  const double*, double, double*, int*, cudaStream_t);
+                                  const double*, const double*, double, double*, int*,
+                                  cudaStream_t);
 template void launch_flux<float>(const DevMesh&, const GeoR<float>&, const KParams<float>&,
-                                 const float*, double, float*, int*, cudaStream_t);
+                                 const float*, const float*, double, float*, int*, cudaStream_t);
 template void launch_gather<double>(const DevMesh&, const Geo64&, const double*, double*, double*,
                                     cudaStream_t);
 template void launch_gather<float>(const DevMesh&, const Geo64&, const float*, double*, double*,
