@@ -28,10 +28,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-stage updates/s, FP32-bulk vs FP64, % roofline at stated error"
 UNIT = "cell-stage/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-FP64_LANES_PER_SM = 2
-SM_MAX_GHZ = 2.07
 
 
 def parse():
@@ -48,6 +44,12 @@ def parse():
     ap.add_argument("--no-vjp", action="store_true", help="skip the residual VJP timing")
     ap.add_argument("--no-implicit", action="store_true",
                     help="skip the implicit (Jacobi) workloads reported beside the headline")
+    ap.add_argument("--no-explosion", action="store_true",
+                    help="skip the spherical-explosion workload reported beside the headline")
+    ap.add_argument("--min-stencil", type=int, default=18,
+                    help="gks_mesh_options.min_stencil of the hybrid meshes (0: as printed)")
+    ap.add_argument("--explosion-n", type=int, default=128, help="cubes per direction")
+    ap.add_argument("--explosion-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -111,13 +113,14 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def workload_desc(n, nc=None, nf=None):
+def workload_desc(n, nc=None, nf=None, min_stencil=0):
     # the hybrid 8-layer pattern has 4 cells and 9.125 faces per cube
     nc = nc if nc is not None else 4 * n ** 3
     nf = nf if nf is not None else 73 * n ** 3 // 8
     return {"workload": f"advection, hybrid layered box {n}^3 cubes ({nc} cells, {nf} faces), "
                         "periodic [0,2]^3, jitter 0.1h seed 1, Euler smooth flux tau=0, CFL 0.5",
             "cells": nc, "faces": nf, "cubes_per_dir": n, "flux": "smooth (Eq. flux-2)",
+            "min_stencil": min_stencil,
             "tau": "zero", "cfl": 0.5, "gamma": 1.4,
             "arithmetic": "FP32; state, face sums and update as float-float pairs (no FP64 "
                           "instructions); FP64 path reported under fp64",
@@ -125,24 +128,34 @@ def workload_desc(n, nc=None, nf=None):
 
 
 # ------------------------------------------------------------------------------ oracle timing
-def time_oracle(n_sample: int, min_seconds: float, max_steps: int | None = None):
-    """Steps of the FP64 CPU oracle on the same generator at n_sample cubes per direction."""
+def host_cores() -> int:
+    """Cores this process may run on (what `nproc` prints)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle(n_sample: int, min_seconds: float, threads: int, min_stencil: int = 0):
+    """S2O4 steps of the FP64 CPU oracle on the same generator at n_sample cubes per direction,
+    with `threads` OpenMP threads, for at least min_seconds. Returns (cells, steps, seconds)."""
     import oracle
     from paper_2203_09047_gb300 import inputs as I
     m = I.layered_box_mesh(n_sample, "hybrid8")
-    om = oracle.Mesh(m)
+    om = oracle.Mesh(m, min_stencil=min_stencil)
     P = oracle.params_vec()
     Q = I.advection_state(m)
     dt = om.max_dt(P, Q, 0.5)
+    oracle.set_threads(threads)
+    Q = om.step(P, Q, dt, 1)  # builds the stencils (lazy parts) outside the timed loop
     steps, t0 = 0, time.perf_counter()
     while True:
         Q = om.step(P, Q, dt, 1)
         steps += 1
         el = time.perf_counter() - t0
-        if (max_steps is not None and steps >= max_steps) or (max_steps is None and el >= min_seconds):
+        if el >= min_seconds:
             break
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return om.n_cells, steps, el, cores
+    return om.n_cells, steps, el
 
 
 def reference_arm(args):
@@ -155,7 +168,9 @@ def reference_arm(args):
     n_sample = 8
     from paper_2203_09047_gb300 import inputs as I
     m = I.layered_box_mesh(n_sample, "hybrid8")
-    om = oracle.Mesh(m)
+    om = oracle.Mesh(m, min_stencil=args.min_stencil)
+    cores = host_cores()
+    oracle.set_threads(cores)
     P = oracle.params_vec()
     Q = I.advection_state(m)
     dt = om.max_dt(P, Q, 0.5)
@@ -167,13 +182,14 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     nc = om.n_cells
     value = nc * 2 * args.steps / el
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = f"{nc}-cell hybrid box (8^3 cubes, same generator) per step"
+    sample = (f"{nc}-cell hybrid box (8^3 cubes, same generator and stencils) per step; the "
+              "oracle's cost per cell-stage does not depend on the mesh size, so the rate stands "
+              f"for the {4 * args.n ** 3}-cell workload")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(args.n),
+            "config": workload_desc(args.n, min_stencil=args.min_stencil),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -271,6 +287,76 @@ def run_implicit(gks, I, stream, torch, kmax=3, steps=20, warmup=3):
     return out
 
 
+def run_explosion(gks, I, stream, torch, args, fp32_peak, hbm):
+    """The Section 5 spherical explosion in the reflecting box [-1,1]^3 on the hybrid generator
+    (full flux, inviscid collision time, nonlinear weights, Gauss-point positivity fallback):
+    mixed-precision and FP64 throughput over the same steps from the same state, the relative
+    mass and energy drift per step, and the mixed-vs-FP64 density difference."""
+    n, K = args.explosion_n, args.explosion_steps
+    m = I.layered_box_mesh(n, "hybrid8", lo=(-1, -1, -1), hi=(1, 1, 1), bc=(1, 1, 1))
+    Q0 = I.explosion_state(m)
+    mesh = gks.Mesh(m, min_stencil=args.min_stencil)
+    params = dict(flux_mode=1, tau_model=1, gp_fallback=1)
+    rec = {"workload": f"spherical explosion, hybrid layered box {n}^3 cubes ({mesh.n_cells} "
+                       f"cells, {mesh.n_faces} faces), reflecting walls [-1,1]^3, full flux, "
+                       "inviscid collision time, CFL 0.5, Gauss-point positivity fallback",
+           "cells": mesh.n_cells, "faces": mesh.n_faces, "steps": K}
+    states, dt, vol = {}, None, None
+    for prec, key in ((gks.GKS_PREC_MIXED, "mixed"), (gks.GKS_PREC_FP64, "fp64")):
+        S = gks.Solver(mesh, stream=stream, precision=prec, **params)
+        S.set_state(Q0)
+        if dt is None:
+            dt = S.max_dt(0.5)
+            _, wq = S.cell_quadrature()
+            vol = wq.sum(axis=1)
+            del wq
+        if prec == gks.GKS_PREC_MIXED:
+            gks.gks_timing_enable(S.h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        gks.gks_step(S.h, dt, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        gks.gks_check(S.h)
+        ms = ev0.elapsed_time(ev1)
+        q = S.get_state().cpu().numpy()
+        states[key] = q
+        r = {"value": mesh.n_cells * 2 * K / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / K}
+        for v, name in ((0, "mass"), (4, "energy")):
+            tot0 = float(vol @ Q0[v])
+            r[f"{name}_drift_per_step"] = abs(float(vol @ q[v]) - tot0) / abs(tot0) / K
+        if prec == gks.GKS_PREC_MIXED:
+            kms, kcnt = gks.gks_timing_read(S.h)
+            bytes_k = gks.gks_kernel_bytes(S.h)
+            fl, _ = gks.gks_flux_opcount(1, 1)
+            names = ["recon", "flux", "gather"]
+            tot = sum(kms)
+            kt = {names[k]: {"launches": kcnt[k], "avg_ms": kms[k] / max(kcnt[k], 1),
+                             "share": kms[k] / tot if tot else None} for k in range(3)}
+            for k in range(3):
+                kt[names[k]]["gbs"] = bytes_k[k] / (kt[names[k]]["avg_ms"] * 1e-3) / 1e9
+            kt["flux"]["tflops"] = fl * 4 * mesh.n_faces / (kt["flux"]["avg_ms"] * 1e-3) / 1e12
+            r["kernels"] = kt
+            dom = max(kt, key=lambda k: kt[k]["share"] or 0)
+            if dom == "flux":
+                r["roofline"] = {"kernel": "k_flux<float, full>", "bound": "alu",
+                                 "achieved": kt["flux"]["tflops"], "peak": fp32_peak,
+                                 "unit": "TFLOP/s", "frac": kt["flux"]["tflops"] / fp32_peak,
+                                 "flops_per_gauss_point": fl}
+            else:
+                r["roofline"] = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": kt[dom]["gbs"],
+                                 "peak": hbm, "unit": "GB/s", "frac": kt[dom]["gbs"] / hbm}
+        rec[key] = r
+        S.close()
+    d = np.abs(states["mixed"][0] - states["fp64"][0])
+    rec["mixed_vs_fp64_L1_rho"] = float(vol @ d / vol.sum())
+    rec["mixed_vs_fp64_L1_rho_rel"] = float(vol @ d / (vol @ states["fp64"][0]))
+    rec["dt"] = dt
+    mesh.close()
+    return rec
+
+
 def run_gpu(args):
     import torch
 
@@ -292,7 +378,7 @@ def run_gpu(args):
 
     mesh_dict = I.layered_box_mesh(args.n, "hybrid8")
     Q0 = I.advection_state(mesh_dict)
-    mesh = gks.Mesh(mesh_dict)
+    mesh = gks.Mesh(mesh_dict, min_stencil=args.min_stencil)
     stream = torch.cuda.Stream()
     results = {}
 
@@ -334,7 +420,18 @@ def run_gpu(args):
     fp64 = measure(gks.GKS_PREC_FP64, fp64_steps, 2)
     v64 = nc * 2 * fp64_steps / (fp64["ms"] * 1e-3)
 
-    # error of the mixed path against the FP64 path after the same steps from the same state
+    # the FP64-update mixed mode (FP32 reconstruction and flux, FP64 face sums and update)
+    upd_steps = max(3, args.steps // 4)
+    upd = measure(gks.GKS_PREC_MIXED_FP64UPD, upd_steps, 2, timed_kernels=False)
+    v_upd = nc * 2 * upd_steps / (upd["ms"] * 1e-3)
+    upd["solver"].close()
+
+    # errors of the mixed modes against the FP64 path after the same steps from the same state,
+    # and the conservation drift of each mode (volume-weighted totals of mass and energy)
+    xq, wq = mixed["solver"].cell_quadrature()
+    vol = wq.sum(axis=1)
+    del xq, wq
+
     def advance(precision, k):
         T = gks.Solver(mesh, stream=stream, precision=precision)
         T.set_state(Q0)
@@ -342,16 +439,22 @@ def run_gpu(args):
         out = T.get_state().double().cpu().numpy()
         T.close()
         return out
+
+    def drift(q):
+        return {name: float(abs(vol @ q[v] - vol @ Q0[v]) / abs(vol @ Q0[v]))
+                for v, name in ((0, "mass"), (4, "energy"))}
     k_err = 10
     qm, qd = advance(gks.GKS_PREC_MIXED, k_err), advance(gks.GKS_PREC_FP64, k_err)
+    qu = advance(gks.GKS_PREC_MIXED_FP64UPD, k_err)
     err = float(np.linalg.norm(qm - qd) / np.linalg.norm(qd))
+    err_upd = float(np.linalg.norm(qu - qd) / np.linalg.norm(qd))
 
-    # rooflines
+    # rooflines: HBM copy bandwidth from MEASURED_PEAKS.json; FP32 and FP64 FMA throughput
+    # measured now on this GPU (gks_alu_peaks)
     bytes_k = gks.gks_kernel_bytes(S.h)
     hbm, hbm_src = peaks()
     flops_gp, special_gp = gks.gks_flux_opcount(0, 0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_GHZ * 1e-3  # TFLOP/s
-    fp64_peak = SM_COUNT * FP64_LANES_PER_SM * 2 * SM_MAX_GHZ * 1e-3
+    fp32_peak, fp64_peak = gks.gks_alu_peaks()  # TFLOP/s
 
     def kernel_table(res, is_mixed):
         names = ["recon", "flux", "gather"]
@@ -387,8 +490,8 @@ def run_gpu(args):
             return {"kernel": f"k_flux<{'float' if is_mixed else 'double'}>", "bound": "alu",
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                     "traffic": (dram_per_unit["flux"][0] * dram_per_unit["flux"][1]) if is_mixed else None,
-                    "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM if is_mixed else FP64_LANES_PER_SM}"
-                                   f" {'FP32' if is_mixed else 'FP64'} FMA lanes x 2 x {SM_MAX_GHZ} GHz",
+                    "peak_source": f"measured {'FP32' if is_mixed else 'FP64'} FMA throughput of "
+                                   "this GPU (gks_alu_peaks, an FMA as 2 flops)",
                     "flops_per_gauss_point": flops_gp, "special_per_gauss_point": special_gp}
         ach = table[dom]["gbs"]
         traffic = None
@@ -411,8 +514,18 @@ def run_gpu(args):
         "fp64": {"value": v64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64["ms"] / fp64_steps,
                  "dtype": "f64", "roofline": roof_for(kt64, False), "kernels": kt64,
                  "clocks": fp64["clocks"]},
-        "error": {"mixed_vs_fp64_state_rel_l2": err, "after_steps": k_err,
+        "fp64_update": {"value": v_upd, "unit": UNIT, "steps": upd_steps,
+                        "ms_per_step": upd["ms"] / upd_steps, "dtype": "f32 + f64 update",
+                        "mode": "GKS_PREC_MIXED_FP64UPD: FP32 reconstruction and flux, FP64 face "
+                                "sums and FP64 update of an FP64 state",
+                        "clocks": upd["clocks"]},
+        "error": {"mixed_vs_fp64_state_rel_l2": err,
+                  "fp64_update_vs_fp64_state_rel_l2": err_upd, "after_steps": k_err,
+                  "drift_after_steps": {"mixed": drift(qm), "fp64_update": drift(qu),
+                                        "fp64": drift(qd)},
                   "fp64_vs_oracle": "<= 1e-12 relative L2 (parity tests)"},
+        "alu_peaks_tflops": {"fp32": fp32_peak, "fp64": fp64_peak,
+                             "source": "gks_alu_peaks, measured in this run"},
     }
     if world > 1:
         line["parallelism"] = f"{world} independent replicas (one full mesh per GPU)"
@@ -444,13 +557,23 @@ def run_gpu(args):
     if not args.no_implicit:
         line["implicit"] = run_implicit(gks, I, stream, torch)
 
+    # the spherical explosion (largest configuration) beside the headline
+    if not args.no_explosion:
+        line["explosion"] = run_explosion(gks, I, stream, torch, args, fp32_peak, hbm)
+
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         import oracle
         oracle.build()
-        n_s, steps_s, el_s, cores = time_oracle(16, 10.0)
-        line["cpu_baseline"] = {"value": n_s * 2 * steps_s / el_s, "unit": UNIT, "cores": cores,
-                                "kind": "oracle",
-                                "sample": f"{steps_s} S2O4 steps on the {n_s}-cell 16^3-cube mesh of the same generator"}
+        cores = host_cores()
+        n_s, steps_a, el_a = time_oracle(16, 10.0, cores, args.min_stencil)
+        _, steps_1, el_1 = time_oracle(16, 10.0, 1, args.min_stencil)
+        line["cpu_baseline"] = {
+            "value": n_s * 2 * steps_a / el_a, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1core": n_s * 2 * steps_1 / el_1,
+            "sample": f"{steps_a} S2O4 steps ({cores} threads) and {steps_1} steps (1 thread) on "
+                      f"the {n_s}-cell 16^3-cube mesh of the same generator and stencils; the "
+                      "oracle's cost per cell-stage does not depend on the mesh size, so the rate "
+                      f"stands for the {nc}-cell workload"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -58,12 +58,16 @@ enum { GKS_FLUX_SMOOTH = 0, GKS_FLUX_FULL = 1 };
  * power law of Section 5.4, mu(T) = mu (T/T_ref)^mu_pow with T = p/rho of the interface
  * equilibrium. */
 enum { GKS_TAU_ZERO = 0, GKS_TAU_INVISCID = 1, GKS_TAU_VISCOUS = 2, GKS_TAU_POWER_LAW = 3 };
-/* Arithmetic: FP64 everywhere, or FP32 reconstruction and flux with the state, the stencil
- * differences, the face sums and the two-stage update in float-float arithmetic (each value an
- * unevaluated sum of two FP32 numbers, about 48 significant bits; error-free TwoSum and FMA
- * TwoProduct), which conserves mass, momentum and energy to about 2^-46 relative per update
- * and executes no FP64 instruction on the hot path. */
-enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1 };
+/* Arithmetic: GKS_PREC_FP64, FP64 everywhere. GKS_PREC_MIXED: FP32 reconstruction and flux
+ * with the state, the stencil differences, the face sums and the two-stage update in float-float
+ * arithmetic (each value an unevaluated sum of two FP32 numbers, about 48 significant bits;
+ * error-free TwoSum and FMA TwoProduct), which conserves mass, momentum and energy to about
+ * 2^-46 relative per update and executes no FP64 instruction on the hot path.
+ * GKS_PREC_MIXED_FP64UPD: the same FP32 reconstruction and flux, with FP64 face sums and the
+ * FP64 two-stage update of an FP64 state (the reconstruction reads its float-pair copy);
+ * gks_step keeps that state in FP64 throughout (gks_step_implicit updates the float-pair copy,
+ * as in GKS_PREC_MIXED). */
+enum { GKS_PREC_FP64 = 0, GKS_PREC_MIXED = 1, GKS_PREC_MIXED_FP64UPD = 2 };
 
 typedef struct {
   double gamma;      /* specific heat ratio; K = (5 - 3 gamma)/(gamma - 1) internal dofs */
@@ -132,6 +136,30 @@ gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
                            const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
                            const double lo[3], const double hi[3], gks_mesh** out);
 
+/* Cell order inside the library (the caller's order is kept at the ABI): cells are grouped by
+ * kind, then ordered by the caller's index, the Morton code of the vertex mean (default), or the
+ * reverse Cuthill-McKee order of the face graph. */
+enum { GKS_REORDER_NONE = 0, GKS_REORDER_MORTON = 1, GKS_REORDER_RCM = 2 };
+typedef struct {
+  int reorder;     /* GKS_REORDER_* */
+  int min_stencil; /* 0: the big stencil of Section 2 as printed (face neighbours and their face
+                      neighbours). n > 0 (a reading, not in the paper; at most 64): a big stencil
+                      with fewer than n members takes the face neighbours of its members, member
+                      by member in stencil order and face by face in face-label order, until it
+                      has n members (images across more than two wall planes are skipped). On the
+                      layered hybrid generator, whose transition layers hold six pyramids sharing
+                      the cube centre and the split-pyramid tetrahedra, the printed stencils give
+                      a linearly unstable reconstruction; 18 (twice the nine unknowns of the
+                      quadratic) removes the instability. */
+} gks_mesh_options;
+
+/* gks_mesh_create with options (opt = NULL: GKS_REORDER_MORTON, min_stencil 0). Errors as
+ * gks_mesh_create, and GKS_E_INVAL for an unknown reorder or min_stencil outside [0, 64]. */
+gks_status gks_mesh_create_ex(int64_t n_nodes, const double* xyz, int64_t n_cells,
+                              const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
+                              const double lo[3], const double hi[3],
+                              const gks_mesh_options* opt, gks_mesh** out);
+
 /* Counts of a built mesh: cells, faces, total stencil entries. */
 gks_status gks_mesh_counts(const gks_mesh* m, int64_t* n_cells, int64_t* n_faces,
                            int64_t* n_stencil);
@@ -180,6 +208,22 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps);
 /* Synchronise the stream and report GKS_E_NONPHYSICAL if any earlier step or residual met
  * rho <= 0, p <= 0 or NaN (the device flag is then cleared). */
 gks_status gks_check(gks_solver* s);
+
+/* The two stage combinations of gks_step (Section 3.3) on caller arrays, for a rollout built
+ * from gks_residual calls (a differentiable rollout, or a caller's own stepping):
+ *   stage 1: out = Q + dt/2 L + dt^2/8 Lt              (Lts is not read; may be NULL)
+ *   stage 2: out = Q + dt L + dt^2/6 (Lt + 2 Lts)
+ * Q, L, Lt, Lts, out: device pointers to n float64 values each (any layout, the same for all;
+ * out may alias Q); enqueued on `stream` (a cudaStream_t, NULL the legacy stream), not
+ * synchronised. Errors: GKS_E_INVAL (stage not 1 or 2, dt <= 0, n < 0, a missing array), with a
+ * message in gks_last_error(NULL); GKS_E_CUDA. */
+gks_status gks_s2o4_stage(int64_t n, int stage, double dt, const double* Q, const double* L,
+                          const double* Lt, const double* Lts, double* out, void* stream);
+/* The transpose of gks_s2o4_stage: for a cotangent g of out, gQ = g, gL = c1 g, gLt = c2 g and
+ * (stage 2) gLts = 2 c2 g, with c1, c2 = dt/2, dt^2/8 (stage 1) or dt, dt^2/6 (stage 2). Device
+ * pointers to n float64 values; gLts is not written in stage 1 (may be NULL). Same errors. */
+gks_status gks_s2o4_stage_vjp(int64_t n, int stage, double dt, const double* g, double* gQ,
+                              double* gL, double* gLt, double* gLts, void* stream);
 
 /* nsteps implicit steps for steady problems (Section 4, Jacobi iteration): per step the
  * residual averaged over [0, dt], |Omega_i| Res_i = -sum_f s_f int_0^dt F_f dt / dt (the
@@ -243,6 +287,14 @@ gks_status gks_launches_per_pass(const gks_solver* s, int64_t launches[3]);
  * sqrt. Computed on the host by running the kernel's own templated arithmetic with a counting
  * scalar type. Returns 0 on success. Not thread-safe. */
 int gks_flux_opcount(int flux_mode, int tau_model, double* flops, double* special);
+
+/* Measured FP32 and FP64 FMA throughput of the current device in TFLOP/s (an FMA counts as two
+ * flops): independent FMA chains in every thread of a grid of several waves, timed with CUDA
+ * events on an internal stream; the denominators of the ALU-bound flux rooflines. A utility of
+ * this library (the paper has no counterpart). Allocates and frees 8 bytes of device memory
+ * and synchronises the device's work on its own stream. Errors: GKS_E_INVAL, GKS_E_CUDA (text in
+ * gks_last_error(NULL)). */
+gks_status gks_alu_peaks(double* fp32_tflops, double* fp64_tflops);
 
 /* Allocation-free CFL time-step bound, for callers that cannot call cudaMalloc: processes
  * whose device memory is owned by another allocator (a framework pool that has reserved the

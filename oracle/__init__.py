@@ -70,7 +70,7 @@ def lib():
         L.oracle_mesh_create.argtypes = [ctypes.c_int64, D, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int8),
                                          ctypes.POINTER(ctypes.c_int64), I, D, D, ctypes.c_int,
-                                         I, ctypes.c_char_p, ctypes.c_int]
+                                         ctypes.c_int, I, ctypes.c_char_p, ctypes.c_int]
         L.oracle_mesh_destroy.argtypes = [P]
         L.oracle_n_faces.restype = ctypes.c_int64
         L.oracle_n_faces.argtypes = [P]
@@ -82,6 +82,10 @@ def lib():
         L.oracle_gp_flux.argtypes = [D, D, D, D, D, ctypes.c_double, D]
         L.oracle_weno_detail.argtypes = [P, D, D, ctypes.c_int, D, D, D, D, D, I, D]
         L.oracle_weno_weights.restype = ctypes.c_double
+        L.oracle_set_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_threads.restype = None
+        L.oracle_max_threads.argtypes = []
+        L.oracle_max_threads.restype = ctypes.c_int
         L.oracle_weno_weights.argtypes = [D, ctypes.c_int, D, D]
         L.oracle_time_coeffs.argtypes = [ctypes.c_double, ctypes.c_double, D]
         L.oracle_wall_ghost.argtypes = [D, ctypes.c_int, ctypes.c_int, D, D, D, D]
@@ -116,7 +120,9 @@ class OracleError(RuntimeError):
 class Mesh:
     """The oracle's view of a mesh: topology, geometry and stencils built from the inputs."""
 
-    def __init__(self, mesh: dict, lazy: bool = False):
+    def __init__(self, mesh: dict, lazy: bool = False, min_stencil: int = 0):
+        """min_stencil > 0: big stencils with fewer members take face neighbours of their members
+        (a third ring, in stencil and face-label order) until they have min_stencil."""
         L = lib()
         xyz = np.ascontiguousarray(mesh["xyz"], dtype=np.float64)
         ct = np.ascontiguousarray(mesh["cell_type"], dtype=np.int8)
@@ -129,7 +135,8 @@ class Mesh:
         self.h = L.oracle_mesh_create(len(xyz), _d(xyz), len(ct),
                                       ct.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                                       cn.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _i(bc),
-                                      _d(lo), _d(hi), 1 if lazy else 0, ctypes.byref(st), err, 256)
+                                      _d(lo), _d(hi), 1 if lazy else 0, int(min_stencil),
+                                      ctypes.byref(st), err, 256)
         if not self.h:
             raise OracleError(st.value, err.value.decode())
         self.n_cells = len(ct)
@@ -263,6 +270,15 @@ def gp_flux(params, ql, dql, qr, dqr, dt):
     if st:
         raise OracleError(st)
     return F
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the oracle's loops use from now on."""
+    lib().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
 
 
 def weno_weights(params, beta):

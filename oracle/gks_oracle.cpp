@@ -46,6 +46,8 @@
 //    drops the volume of the residual's definition), Res is the GKS residual averaged over the
 //    step, r_f = max over both sides of |U . n| + c at Q^n, S_f n_f the face's area vector.
 
+#include <omp.h>
+
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -397,6 +399,7 @@ struct Mesh {
   std::vector<Cell> cells;
   std::vector<Face> faces;
   std::string err;
+  int min_stencil = 0;  // big stencils smaller than this take a third ring (0: as printed)
 };
 
 const int ST_OK = 0, ST_INVAL = 1, ST_MESH = 4, ST_SINGULAR = 5, ST_NONPHYS = 6;
@@ -695,6 +698,22 @@ int build_cell_stencil(Mesh& m, int i) {
     for (size_t p = 0; p < ci.nbs.size(); ++p) add(ci.stencil, ci.nbs[p]);
     for (size_t p = 0; p < ci.nbs.size(); ++p)
       for (const Member& mb : second_ring((int)p)) add(ci.stencil, mb);
+    // Reading (not in the paper): a big stencil with fewer than min_stencil members takes the
+    // face neighbours of its members, member by member in stencil order and face by face in
+    // face-label order, until it has min_stencil members, skipping images that cross more than
+    // two wall planes.
+    if ((int)ci.stencil.size() < m.min_stencil) {
+      const size_t n2 = ci.stencil.size();
+      for (size_t k = 0; k < n2 && (int)ci.stencil.size() < m.min_stencil; ++k) {
+        const Member mk = ci.stencil[k];
+        const Cell& cj = m.cells[mk.cell];
+        for (size_t q = 0; q < cj.nbs.size() && (int)ci.stencil.size() < m.min_stencil; ++q) {
+          const Xform T = compose(mk.T, cj.nbs[q].T);
+          if (T.nw > 2) continue;
+          add(ci.stencil, Member{cj.nbs[q].cell, T});
+        }
+      }
+    }
     ci.plain = true;
     for (const Member& mb : ci.stencil)
       if (!is_identity(mb.T, tol)) ci.plain = false;
@@ -1637,9 +1656,10 @@ extern "C" {
 // sampled residual on large meshes).
 void* oracle_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
                          const int8_t* cell_type, const int64_t* cell_nodes, const int* bc,
-                         const double* lo, const double* hi, int lazy, int* status, char* errbuf,
-                         int errlen) {
+                         const double* lo, const double* hi, int lazy, int min_stencil,
+                         int* status, char* errbuf, int errlen) {
   Mesh* m = new Mesh;
+  m->min_stencil = min_stencil;
   m->n_nodes = (int)n_nodes;
   m->n_cells = (int)n_cells;
   m->xyz.assign(xyz, xyz + 3 * n_nodes);
@@ -1803,6 +1823,11 @@ int oracle_weno_detail(void* h, const double* params, const double* Q, int cell,
   }
   return ST_OK;
 }
+
+// OpenMP threads of the oracle's loops over cells and faces (for timing it on 1 core and on
+// all cores).
+void oracle_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int oracle_max_threads() { return omp_get_max_threads(); }
 
 // The nonlinear weights alone, from given indicators beta[0..M]: wbar[0..M]; returns tau.
 double oracle_weno_weights(const double* params, int M, const double* beta, double* wbar) {

@@ -24,7 +24,7 @@ STATUS_NAMES = ["GKS_OK", "GKS_E_INVAL", "GKS_E_NOMEM", "GKS_E_CUDA", "GKS_E_MES
 GKS_FLUX_SMOOTH, GKS_FLUX_FULL = 0, 1
 GKS_TAU_ZERO, GKS_TAU_INVISCID, GKS_TAU_VISCOUS, GKS_TAU_POWER_LAW = 0, 1, 2, 3
 GKS_BC_PERIODIC, GKS_BC_REFLECT, GKS_BC_NOSLIP, GKS_BC_FARFIELD = 0, 1, 2, 3
-GKS_PREC_FP64, GKS_PREC_MIXED = 0, 1
+GKS_PREC_FP64, GKS_PREC_MIXED, GKS_PREC_MIXED_FP64UPD = 0, 1, 2
 
 
 class gks_params(ctypes.Structure):
@@ -36,6 +36,13 @@ class gks_params(ctypes.Structure):
                 ("T_ref", ctypes.c_double), ("mu_pow", ctypes.c_double),
                 ("wall_u", (ctypes.c_double * 3) * 6), ("wall_T", ctypes.c_double * 6),
                 ("farfield", (ctypes.c_double * 5) * 6), ("gp_fallback", ctypes.c_int)]
+
+
+GKS_REORDER_NONE, GKS_REORDER_MORTON, GKS_REORDER_RCM = 0, 1, 2
+
+
+class gks_mesh_options(ctypes.Structure):
+    _fields_ = [("reorder", ctypes.c_int), ("min_stencil", ctypes.c_int)]
 
 
 class GksError(RuntimeError):
@@ -62,6 +69,9 @@ def load_library(path: str = LIB_PATH):
     L.gks_params_default.restype = None
     L.gks_mesh_create.argtypes = [I64, P, I64, P, P, P, P, P, ctypes.POINTER(P)]
     L.gks_mesh_create.restype = st
+    L.gks_mesh_create_ex.argtypes = [I64, P, I64, P, P, P, P, P, ctypes.POINTER(gks_mesh_options),
+                                     ctypes.POINTER(P)]
+    L.gks_mesh_create_ex.restype = st
     L.gks_mesh_counts.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
     L.gks_mesh_counts.restype = st
     L.gks_mesh_last_error.argtypes = []
@@ -99,6 +109,12 @@ def load_library(path: str = LIB_PATH):
     L.gks_cfl_dt_noalloc.argtypes = [I64, P, P, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, P, P]
     L.gks_cfl_dt_noalloc.restype = st
+    L.gks_alu_peaks.argtypes = [D, D]
+    L.gks_alu_peaks.restype = st
+    L.gks_s2o4_stage.argtypes = [I64, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
+    L.gks_s2o4_stage.restype = st
+    L.gks_s2o4_stage_vjp.argtypes = [I64, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
+    L.gks_s2o4_stage_vjp.restype = st
     for name in ("gks_gp_flux_host", "gks_gp_flux_vjp_host", "gks_gp_face_host"):
         getattr(L, name).restype = ctypes.c_int
     L.gks_wall_ghost_host.argtypes = [P, ctypes.c_int] + [P] * 8
@@ -151,7 +167,8 @@ def gks_params_default(**overrides) -> gks_params:
     return p
 
 
-def gks_mesh_create(xyz, cell_type, cell_nodes, bc, lo, hi) -> ctypes.c_void_p:
+def gks_mesh_create(xyz, cell_type, cell_nodes, bc, lo, hi, reorder: int = GKS_REORDER_MORTON,
+                    min_stencil: int = 0) -> ctypes.c_void_p:
     L = load_library()
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     ct = np.ascontiguousarray(cell_type, dtype=np.int8)
@@ -160,8 +177,10 @@ def gks_mesh_create(xyz, cell_type, cell_nodes, bc, lo, hi) -> ctypes.c_void_p:
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     hi = np.ascontiguousarray(hi, dtype=np.float64)
     out = ctypes.c_void_p()
-    s = L.gks_mesh_create(len(xyz), xyz.ctypes.data, len(ct), ct.ctypes.data, cn.ctypes.data,
-                          bc.ctypes.data, lo.ctypes.data, hi.ctypes.data, ctypes.byref(out))
+    opt = gks_mesh_options(int(reorder), int(min_stencil))
+    s = L.gks_mesh_create_ex(len(xyz), xyz.ctypes.data, len(ct), ct.ctypes.data, cn.ctypes.data,
+                             bc.ctypes.data, lo.ctypes.data, hi.ctypes.data, ctypes.byref(opt),
+                             ctypes.byref(out))
     if s != GKS_OK:
         raise GksError(s, L.gks_mesh_last_error().decode())
     return out
@@ -271,6 +290,35 @@ def gks_cfl_dt_noalloc(n_cells: int, Q, h, gamma: float, mu: float, cfl: float, 
         raise GksError(s, L.gks_last_error(None).decode())
 
 
+def gks_alu_peaks():
+    """Measured (FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    s = lib.gks_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if s != GKS_OK:
+        raise GksError(s, lib.gks_last_error(None).decode())
+    return a.value, b.value
+
+
+def gks_s2o4_stage(stage: int, dt: float, Q, L, Lt, Lts, out, stream: int = 0):
+    """out = the stage-1 or stage-2 combination of Section 3.3 (device float64 tensors, same
+    shape; Lts may be None in stage 1)."""
+    lib = load_library()
+    s = lib.gks_s2o4_stage(Q.numel(), stage, dt, _ptr(Q), _ptr(L), _ptr(Lt),
+                           None if Lts is None else _ptr(Lts), _ptr(out), ctypes.c_void_p(stream))
+    if s != GKS_OK:
+        raise GksError(s, lib.gks_last_error(None).decode())
+
+
+def gks_s2o4_stage_vjp(stage: int, dt: float, g, gQ, gL, gLt, gLts, stream: int = 0):
+    """Cotangents of Q, L, Lt (and Lts in stage 2) for a cotangent g of the stage output."""
+    lib = load_library()
+    s = lib.gks_s2o4_stage_vjp(g.numel(), stage, dt, _ptr(g), _ptr(gQ), _ptr(gL), _ptr(gLt),
+                               None if gLts is None else _ptr(gLts), ctypes.c_void_p(stream))
+    if s != GKS_OK:
+        raise GksError(s, lib.gks_last_error(None).decode())
+
+
 def gks_destroy(solver):
     load_library().gks_destroy(solver)
 
@@ -283,9 +331,9 @@ def gks_mesh_destroy(mesh):
 class Mesh:
     """Owns a gks_mesh handle built from an inputs-style mesh dict (host-side topology only)."""
 
-    def __init__(self, mesh: dict):
+    def __init__(self, mesh: dict, reorder: int = GKS_REORDER_MORTON, min_stencil: int = 0):
         self.h = gks_mesh_create(mesh["xyz"], mesh["cell_type"], mesh["cell_nodes"], mesh["bc"],
-                                 mesh["lo"], mesh["hi"])
+                                 mesh["lo"], mesh["hi"], reorder, min_stencil)
         self.n_cells, self.n_faces, self.n_stencil = gks_mesh_counts(self.h)
 
     def close(self):
@@ -305,11 +353,15 @@ class Solver:
     device (or pinned host tensors for host-side transfers). `mesh` is an inputs-style dict or a
     Mesh (which may be shared by several solvers)."""
 
-    def __init__(self, mesh, stream=None, **params):
+    def __init__(self, mesh, stream=None, reorder=None, min_stencil=None, **params):
+        """reorder / min_stencil are mesh options (gks_mesh_options), for a mesh dict only."""
         import torch
         self.torch = torch
         own = not isinstance(mesh, Mesh)
-        M = Mesh(mesh) if own else mesh
+        if not own and (reorder is not None or min_stencil is not None):
+            raise ValueError("reorder and min_stencil belong to the Mesh, which is already built")
+        M = Mesh(mesh, GKS_REORDER_MORTON if reorder is None else reorder,
+                 0 if min_stencil is None else min_stencil) if own else mesh
         self.n_cells, self.n_faces, self.n_stencil = M.n_cells, M.n_faces, M.n_stencil
         self.params = gks_params_default(**params)
         self.stream = stream if stream is not None else torch.cuda.current_stream()

@@ -1,7 +1,9 @@
 """Differentiable residual and two-stage fourth-order time stepping.
 
-GKSResidual wraps gks_residual (forward) and gks_residual_vjp (backward) in a
-torch.autograd.Function. s2o4_rollout advances a state through n S2O4 steps of Section 3.3
+GKSResidual wraps gks_residual (forward) and gks_residual_vjp (backward), and S2O4Stage wraps
+gks_s2o4_stage and its transpose gks_s2o4_stage_vjp, each in a torch.autograd.Function; every
+operation of the rollout runs in the library's kernels, and this module only wires the calls.
+s2o4_rollout advances a state through n S2O4 steps of Section 3.3
   Q* = Q + dt/2 L(Q) + dt^2/8 Lt(Q),  Q' = Q + dt L(Q) + dt^2/6 (Lt(Q) + 2 Lt(Q*))
 with checkpoints every k steps (torch.utils.checkpoint): the backward pass recomputes one segment
 at a time, so memory holds the checkpoints plus one segment's stage states.
@@ -11,7 +13,11 @@ from __future__ import annotations
 import torch
 from torch.utils.checkpoint import checkpoint
 
-from . import gks_residual, gks_residual_vjp
+from . import gks_residual, gks_residual_vjp, gks_s2o4_stage, gks_s2o4_stage_vjp
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
 
 
 class GKSResidual(torch.autograd.Function):
@@ -38,11 +44,32 @@ class GKSResidual(torch.autograd.Function):
         return gQ, None, None
 
 
+class S2O4Stage(torch.autograd.Function):
+    """Stage 1: Q + dt/2 L + dt^2/8 Lt; stage 2: Q + dt L + dt^2/6 (Lt + 2 Lts)."""
+
+    @staticmethod
+    def forward(ctx, Q, L, Lt, Lts, stage, dt):
+        Q, L, Lt = Q.contiguous(), L.contiguous(), Lt.contiguous()
+        Lts = None if Lts is None else Lts.contiguous()
+        out = torch.empty_like(Q)
+        gks_s2o4_stage(stage, dt, Q, L, Lt, Lts, out, _stream())
+        ctx.stage, ctx.dt = stage, dt
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        gQ, gL, gLt = torch.empty_like(g), torch.empty_like(g), torch.empty_like(g)
+        gLts = torch.empty_like(g) if ctx.stage == 2 else None
+        gks_s2o4_stage_vjp(ctx.stage, ctx.dt, g, gQ, gL, gLt, gLts, _stream())
+        return gQ, gL, gLt, gLts, None, None
+
+
 def s2o4_step(Q, solver, dt):
     L, Lt = GKSResidual.apply(Q, solver, dt)
-    Qs = Q + (0.5 * dt) * L + (dt * dt / 8.0) * Lt
+    Qs = S2O4Stage.apply(Q, L, Lt, None, 1, dt)
     _, Lts = GKSResidual.apply(Qs, solver, dt)
-    return Q + dt * L + (dt * dt / 6.0) * (Lt + 2.0 * Lts)
+    return S2O4Stage.apply(Q, L, Lt, Lts, 2, dt)
 
 
 def _segment(Q, solver, dt, n):

@@ -33,7 +33,7 @@ def _exact_advection(t, gamma=1.4):
 
 
 def advection(ns=(8, 16, 32, 64), t_end=0.2, cfl=0.5, layers="hybrid8", jitter=0.1,
-              precisions=("fp64", "mixed"), **weno):
+              precisions=("fp64", "mixed"), min_stencil=0, **weno):
     """Section 5.1 accuracy test on the hybrid generator: errors against the exact cell averages
     (volume-weighted, unnormalised L1 and L2 of density as in Tables tab-3d-1/2), orders, and
     cell-stage updates/s, for the FP64 and mixed paths. jitter is the node displacement in units
@@ -51,10 +51,11 @@ def advection(ns=(8, 16, 32, 64), t_end=0.2, cfl=0.5, layers="hybrid8", jitter=0
         for n in ns:
             m = I.layered_box_mesh(n, layers, jitter=jitter)
             try:
-                S = Solver(m, precision=prec, **weno)
+                S = Solver(m, precision=prec, min_stencil=min_stencil, **weno)
             except GksError as e:
                 _emit({"case": "advection", "mesh": layers, "precision": name, "cubes": n,
-                       "jitter": jitter, **weno, "status": f"init: {e}"})
+                       "jitter": jitter, "min_stencil": min_stencil, **weno,
+                       "status": f"init: {e}"})
                 prev = None
                 continue
             Q0 = S.cell_average(_exact_advection(0.0))
@@ -68,7 +69,8 @@ def advection(ns=(8, 16, 32, 64), t_end=0.2, cfl=0.5, layers="hybrid8", jitter=0
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             rec = {"case": "advection", "mesh": layers, "precision": name, "cubes": n,
-                   "cells": S.n_cells, "jitter": jitter, **weno, "steps": nsteps, "dt": dt}
+                   "cells": S.n_cells, "jitter": jitter, "min_stencil": min_stencil, **weno,
+                   "steps": nsteps, "dt": dt}
             try:
                 S.check()
             except GksError as e:
@@ -306,7 +308,7 @@ RIEMANN = {  # Section 5 (Riemann problems): left and right (rho, u, p), split a
 
 
 def riemann(problem="sod", mesh="hex", nx=100, cfl=0.5, flux_mode=1, tau_model=1, jitter=0.0,
-            **weno):
+            min_stencil=0, **weno):
     """The paper's Riemann-problem setup (Section 5): [0,1] x [0,0.1] x [0,0.1] with h = 1/nx,
     non-reflecting x ends (far-field planes holding the left and right states), reflecting y
     and z walls; meshes: nx x nx/10 x nx/10 hexahedra, the same cubes cut into Kuhn tetrahedra,
@@ -325,7 +327,7 @@ def riemann(problem="sod", mesh="hex", nx=100, cfl=0.5, flux_mode=1, tau_model=1
         layers = (mesh,) * nz
     m = I.layered_box_mesh(nz, layers, lo=(0, 0, 0), hi=(1, 0.1, 0.1), bc=(3, 1, 1),
                            jitter=jitter, shape=(nx, nz))
-    M = Mesh(m)
+    M = Mesh(m, min_stencil=min_stencil)
     x = I.vertex_mean(m)
     left = x[:, 0] < 0.5
     rho0 = np.where(left, rl, rr)
@@ -340,7 +342,7 @@ def riemann(problem="sod", mesh="hex", nx=100, cfl=0.5, flux_mode=1, tau_model=1
     for prec, name in ((GKS_PREC_FP64, "fp64"), (GKS_PREC_MIXED, "mixed")):
         rec = {"case": "riemann", "problem": problem, "mesh": mesh, "precision": name, "nx": nx,
                "cells": M.n_cells, "flux_mode": flux_mode, "tau_model": tau_model, "cfl": cfl,
-               "t_end": t_end, "jitter": jitter, **weno}
+               "t_end": t_end, "jitter": jitter, "min_stencil": min_stencil, **weno}
         try:
             S = Solver(M, precision=prec, flux_mode=flux_mode, tau_model=tau_model, farfield=far,
                        **weno)
@@ -493,7 +495,8 @@ def couette(n=8, mu=0.05, mach=0.15, steps=3000, every=500, cfl=2.0, kmax=3, flu
     return rec
 
 
-def explosion(n=32, t_end=0.25, cfl=0.5, chunk=5, gp_fallback=1, precisions=("fp64", "mixed")):
+def explosion(n=32, t_end=0.25, cfl=0.5, chunk=5, gp_fallback=1, precisions=("fp64", "mixed"),
+              min_stencil=18):
     """Spherical explosion in the reflecting box [-1,1]^3 on the hybrid generator (full flux,
     inviscid collision time, WENO nonlinear weights): inside r < 0.4 rho = p = 1, outside
     rho = 0.125, p = 0.1, at rest. The FP64 run takes dt = CFL-bounded every `chunk` steps and the
@@ -507,11 +510,11 @@ def explosion(n=32, t_end=0.25, cfl=0.5, chunk=5, gp_fallback=1, precisions=("fp
     if isinstance(precisions, str):
         precisions = tuple(precisions.split(","))
     m = I.layered_box_mesh(n, "hybrid8", lo=(-1, -1, -1), hi=(1, 1, 1), bc=(1, 1, 1))
-    mesh = Mesh(m)
+    mesh = Mesh(m, min_stencil=min_stencil)
     Q0 = I.explosion_state(m)
     params = dict(flux_mode=1, tau_model=1, gp_fallback=gp_fallback)
     base = {"case": "explosion", "cubes": n, "cells": mesh.n_cells, "faces": mesh.n_faces,
-            "t_end": t_end, "cfl": cfl, "gp_fallback": gp_fallback}
+            "t_end": t_end, "cfl": cfl, "gp_fallback": gp_fallback, "min_stencil": min_stencil}
     out, states, dts = [], {}, None
     for prec, name in ((GKS_PREC_FP64, "fp64"), (GKS_PREC_MIXED, "mixed")):
         if name not in precisions:

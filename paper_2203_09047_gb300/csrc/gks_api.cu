@@ -42,6 +42,7 @@ struct gks_solver {
   GeoR<double> gd;
   GeoR<float> gf;
   bool mixed = false;
+  bool fp64upd = false;     // GKS_PREC_MIXED_FP64UPD: Q (FP64) is the master state of the steps
   // buffers (internal order)
   // The state lives in the gather copy QA (FP64 values, or float-float pairs on the FP32 path);
   // Q is its FP64 [5][nc] form, refreshed from QA when a call needs it (q_stale after steps).
@@ -217,7 +218,7 @@ void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode
     launch_gather<R>(s->m, s->g, (const R*)s->fface, L, Lt, s->st);
   else
     launch_stage<R>(s->m, g, (const R*)s->fface, mode, dt, L, Lt, (R*)s->QA, (R*)s->QsA,
-                    s->flag, s->st);
+                    s->flag, s->st, s->fp64upd ? s->Q : nullptr, s->g.ivol);
   s->tock(t);
 }
 
@@ -405,7 +406,11 @@ bool valid_params(const gks_params* p, std::string& why) {
   if (!(p->weno_gamma > 0.0 && p->weno_gamma * 8 < 1.0)) { why = "weno_gamma must lie in (0, 1/8)"; return false; }
   if (!(p->weno_eps > 0.0)) { why = "weno_eps must be > 0"; return false; }
   if (p->weno_pow < 1 || p->weno_pow > 4) { why = "weno_pow must be 1..4"; return false; }
-  if (p->precision != GKS_PREC_FP64 && p->precision != GKS_PREC_MIXED) { why = "precision"; return false; }
+  if (p->precision != GKS_PREC_FP64 && p->precision != GKS_PREC_MIXED &&
+      p->precision != GKS_PREC_MIXED_FP64UPD) {
+    why = "precision";
+    return false;
+  }
   return true;
 }
 
@@ -488,13 +493,24 @@ void gks_params_default(gks_params* p) {
 gks_status gks_mesh_create(int64_t n_nodes, const double* xyz, int64_t n_cells,
                            const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
                            const double lo[3], const double hi[3], gks_mesh** out) {
+  return gks_mesh_create_ex(n_nodes, xyz, n_cells, cell_type, cell_nodes, bc, lo, hi, nullptr,
+                            out);
+}
+
+gks_status gks_mesh_create_ex(int64_t n_nodes, const double* xyz, int64_t n_cells,
+                              const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
+                              const double lo[3], const double hi[3],
+                              const gks_mesh_options* opt, gks_mesh** out) {
   if (!out) return GKS_E_INVAL;
   *out = nullptr;
+  const int reorder = opt ? opt->reorder : GKS_REORDER_MORTON;
+  const int min_stencil = opt ? opt->min_stencil : 0;
   gks_mesh* m = new (std::nothrow) gks_mesh;
   if (!m) return GKS_E_NOMEM;
   gks_status st;
   try {
-    st = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_nodes, bc, lo, hi, m->h, g_mesh_err);
+    st = build_host_mesh(n_nodes, xyz, n_cells, cell_type, cell_nodes, bc, lo, hi, reorder,
+                         min_stencil, m->h, g_mesh_err);
   } catch (const std::bad_alloc&) {
     g_mesh_err = "host allocation failed";
     st = GKS_E_NOMEM;
@@ -533,7 +549,8 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
   if (!s) return GKS_E_NOMEM;
   s->prm = *p;
   s->st = (cudaStream_t)stream;
-  s->mixed = p->precision == GKS_PREC_MIXED;
+  s->mixed = p->precision == GKS_PREC_MIXED || p->precision == GKS_PREC_MIXED_FP64UPD;
+  s->fp64upd = p->precision == GKS_PREC_MIXED_FP64UPD;
   cudaGetDevice(&s->device);
   const HostMesh& h = mesh->h;
   DevMesh& m = s->m;
@@ -735,14 +752,50 @@ gks_status gks_max_dt(gks_solver* s, double cfl, double* dt) {
 
 gks_status gks_step(gks_solver* s, double dt, int nsteps) {
   if (!s || !(dt > 0) || nsteps < 0) return GKS_E_INVAL;
+  if (s->fp64upd) sync_q(s);  // after implicit steps the float-pair copy is the newer state
   for (int k = 0; k < nsteps; ++k) {
     // stage 1 on Q^n (QA): L, Lt kept, Q* to QsA; stage 2 on Q*: Q^{n+1} written into QA
     residual_any(s, s->QA, dt, 1, s->L, s->Lt);
     residual_any(s, s->QsA, dt, 2, s->L, s->Lt);
   }
-  if (nsteps > 0) s->q_stale = true;
+  // the FP64-update mode writes its FP64 state in place; the others update the gather copy
+  if (nsteps > 0 && !s->fp64upd) s->q_stale = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
+}
+
+gks_status gks_s2o4_stage(int64_t n, int stage, double dt, const double* Q, const double* L,
+                          const double* Lt, const double* Lts, double* out, void* stream) {
+  if (n < 0 || (stage != 1 && stage != 2) || !(dt > 0) || (n > 0 && (!Q || !L || !Lt || !out)) ||
+      (n > 0 && stage == 2 && !Lts)) {
+    set_global_error("gks_s2o4_stage: invalid argument");
+    return GKS_E_INVAL;
+  }
+  if (n == 0) return GKS_OK;
+  launch_s2o4_stage(n, stage, dt, Q, L, Lt, Lts, out, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error((std::string("gks_s2o4_stage: ") + cudaGetErrorString(e)).c_str());
+    return GKS_E_CUDA;
+  }
+  return GKS_OK;
+}
+
+gks_status gks_s2o4_stage_vjp(int64_t n, int stage, double dt, const double* g, double* gQ,
+                              double* gL, double* gLt, double* gLts, void* stream) {
+  if (n < 0 || (stage != 1 && stage != 2) || !(dt > 0) ||
+      (n > 0 && (!g || !gQ || !gL || !gLt)) || (n > 0 && stage == 2 && !gLts)) {
+    set_global_error("gks_s2o4_stage_vjp: invalid argument");
+    return GKS_E_INVAL;
+  }
+  if (n == 0) return GKS_OK;
+  launch_s2o4_stage_vjp(n, stage, dt, g, gQ, gL, gLt, gLts, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error((std::string("gks_s2o4_stage_vjp: ") + cudaGetErrorString(e)).c_str());
+    return GKS_E_CUDA;
+  }
+  return GKS_OK;
 }
 
 gks_status gks_step_implicit(gks_solver* s, double dt, int nsteps, int kmax) {
@@ -864,9 +917,11 @@ gks_status gks_kernel_bytes(const gks_solver* s, double bytes[3]) {
   // flux: face cells and wall flag, Gauss data, polynomials read, face fluxes written
   bytes[1] = 9.0 * nf + 40.0 * r * nf + kPolyStride * r * nc + kFaceStride * r * nf;
   // face sums + stage update: CSR, face fluxes, 1/|Omega| (8 B), the state's gather copy read,
-  // L and Lt (written by stage 1, read by stage 2, 8 B per value), the new gather copy written
-  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + kFaceStride * r * nf + 8.0 * nc + 48.0 * nc + 80.0 * nc +
-             48.0 * nc;
+  // L and Lt (written by stage 1, read by stage 2, 8 B per value), the new gather copy written;
+  // the FP64-update mode reads the FP64 state (40 B) in place of the gather copy and writes it
+  // back in stage 2 (half of the passes: 20 B per pass on average)
+  bytes[2] = 4.0 * (nc + 1) + 4.0 * ncf + kFaceStride * r * nf + 8.0 * nc +
+             (s->fp64upd ? 60.0 : 48.0) * nc + 80.0 * nc + 48.0 * nc;
   return GKS_OK;
 }
 

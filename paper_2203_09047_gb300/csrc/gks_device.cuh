@@ -176,12 +176,20 @@ void launch_flux(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const 
 template <class R>
 void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, double* Lt,
                    cudaStream_t st);
+// Two-stage combinations on caller arrays (gks_s2o4_stage, gks_s2o4_stage_vjp).
+void launch_s2o4_stage(int64_t n, int stage, double dt, const double* Q, const double* L,
+                       const double* Lt, const double* Lts, double* out, cudaStream_t st);
+void launch_s2o4_stage_vjp(int64_t n, int stage, double dt, const double* g, double* gQ,
+                           double* gL, double* gLt, double* gLts, cudaStream_t st);
 // One stage of the fourth-order update on the gather copy QA, which holds the state:
 // stage 1 stores L, Lt (FP64 values, or float-float pairs in the same 8 bytes on the FP32 path)
 // and writes Q* to QsA; stage 2 reads them and writes Q^{n+1} to QA.
+// Q64 != nullptr (FP32 path only): FP64 face sums and update of the FP64 master state Q64
+// [5][nc] with the FP64 inverse volumes ivol64, L and Lt in FP64.
 template <class R>
 void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage, double dt,
-                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st);
+                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st,
+                  double* Q64 = nullptr, const double* ivol64 = nullptr);
 // Implicit step (Section 4) on the gather copy QA (the state), after the reconstruction and
 // flux of Q^n: jacobi_init forms |Omega| Res = s + dt/2 st from the face sums, the diagonal
 // D = |Omega|/dt + 1/2 sum_f r_f S_f, the per-entry factors hrs = 1/2 r_f S_f (cell-face CSR

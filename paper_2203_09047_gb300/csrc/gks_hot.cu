@@ -657,6 +657,50 @@ __global__ void __launch_bounds__(256) k_stage_f(
   if (!(q[0].h > 0.f && q[0].h * q[4].h > 0.5f * m2)) atomicOr(flag, kErrNonphysical);
 }
 
+// FP32 reconstruction and flux with the FP64 update (GKS_PREC_MIXED_FP64UPD): the face sums
+// accumulate the FP32 face fluxes in FP64, and the update reads and writes the FP64 state
+// [5][nc], which is the master copy in this mode; the gather copies the reconstruction reads
+// (float pairs) are written from it: Q* by stage 1, Q^{n+1} by stage 2.
+template <bool kSecond>
+__global__ void __launch_bounds__(256) k_stage_fd(
+    int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
+    const float* __restrict__ fface, const double* __restrict__ ivol, double c1, double c2,
+    double* __restrict__ L, double* __restrict__ Lt, double* __restrict__ Q,
+    float* __restrict__ QA, float* __restrict__ QsA, int* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nc) return;
+  double s[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) s[q] = 0.0;
+  for (int k = cf_ptr[i]; k < cf_ptr[i + 1]; ++k) {
+    const int32_t e = __ldg(cf_idx + k);
+    const float4* fp = reinterpret_cast<const float4*>(fface + (int64_t)kFaceStride * (e >> 1));
+    const float4 a = __ldg(fp), b = __ldg(fp + 1), c = __ldg(fp + 2);
+    const float x[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
+    const double sg = (e & 1) ? 1.0 : -1.0;
+#pragma unroll
+    for (int q = 0; q < 10; ++q) s[q] += sg * (double)x[q];
+  }
+  const double iv = ivol[i];
+  double q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double qn = Q[v * nc + i];
+    const double lt = s[5 + v] * iv;
+    if (!kSecond) {
+      const double l = s[v] * iv;
+      L[v * nc + i] = l;
+      Lt[v * nc + i] = lt;
+      q[v] = qn + c1 * l + c2 * lt;
+    } else {
+      q[v] = qn + c1 * L[v * nc + i] + c2 * (Lt[v * nc + i] + 2.0 * lt);
+      Q[v * nc + i] = q[v];
+    }
+  }
+  Gq<float>::store(kSecond ? QA : QsA, i, q);
+  if (!physical(q)) atomicOr(flag, kErrNonphysical);
+}
+
 template <bool kSecond>
 __global__ void __launch_bounds__(256) k_stage_d(
     int64_t nc, const int32_t* __restrict__ cf_ptr, const int32_t* __restrict__ cf_idx,
@@ -685,6 +729,36 @@ __global__ void __launch_bounds__(256) k_stage_d(
   }
   Gq<double>::store(kSecond ? QA : QsA, i, q);
   if (!physical(q)) atomicOr(flag, kErrNonphysical);
+}
+
+// ------------------------------------------------------------------------------------------
+// The two-stage combinations of Section 3.3 on caller arrays of n values, for a differentiable
+// rollout built from residual calls: stage 1 out = Q + c1 L + c2 Lt (c1 = dt/2, c2 = dt^2/8),
+// stage 2 out = Q + c1 L + c2 (Lt + 2 Lts) (c1 = dt, c2 = dt^2/6); and their transposes.
+__global__ void __launch_bounds__(256) k_s2o4_stage(int64_t n, int stage, double c1, double c2,
+                                                    const double* __restrict__ Q,
+                                                    const double* __restrict__ L,
+                                                    const double* __restrict__ Lt,
+                                                    const double* __restrict__ Lts,
+                                                    double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double lt = stage == 1 ? Lt[i] : Lt[i] + 2.0 * Lts[i];
+  out[i] = Q[i] + c1 * L[i] + c2 * lt;
+}
+__global__ void __launch_bounds__(256) k_s2o4_stage_vjp(int64_t n, int stage, double c1,
+                                                        double c2, const double* __restrict__ g,
+                                                        double* __restrict__ gQ,
+                                                        double* __restrict__ gL,
+                                                        double* __restrict__ gLt,
+                                                        double* __restrict__ gLts) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double gi = g[i];
+  gQ[i] = gi;
+  gL[i] = c1 * gi;
+  gLt[i] = c2 * gi;
+  if (stage == 2) gLts[i] = 2.0 * c2 * gi;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1152,11 +1226,23 @@ void launch_gather(const DevMesh& m, const Geo64& g, const R* fface, double* L, 
 }
 template <class R>
 void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage, double dt,
-                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st) {
+                  void* L, void* Lt, R* QA, R* QsA, int* flag, cudaStream_t st, double* Q64,
+                  const double* ivol64) {
   const unsigned nb = blocks_for(m.nc, 256);
   // stage 1: c1 = dt/2, c2 = dt^2/8; stage 2: c1 = dt, c2 = dt^2/6
   const double c1 = stage == 1 ? 0.5 * dt : dt, c2 = stage == 1 ? dt * dt / 8.0 : dt * dt / 6.0;
   if constexpr (std::is_same<R, float>::value) {
+    if (Q64) {  // FP64 update of the FP64 master state
+      double* l = static_cast<double*>(L);
+      double* lt = static_cast<double*>(Lt);
+      if (stage == 1)
+        k_stage_fd<false><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, ivol64, c1, c2, l,
+                                              lt, Q64, QA, QsA, flag);
+      else
+        k_stage_fd<true><<<nb, 256, 0, st>>>(m.nc, m.cf_ptr, m.cf_idx, fface, ivol64, c1, c2, l,
+                                             lt, Q64, QA, QsA, flag);
+      return;
+    }
     ff* l = static_cast<ff*>(L);
     ff* lt = static_cast<ff*>(Lt);
     const ff* iv = reinterpret_cast<const ff*>(g.ivol);
@@ -1177,6 +1263,17 @@ void launch_stage(const DevMesh& m, const GeoR<R>& g, const R* fface, int stage,
                                           QA, QsA, flag);
   }
 }
+void launch_s2o4_stage(int64_t n, int stage, double dt, const double* Q, const double* L,
+                       const double* Lt, const double* Lts, double* out, cudaStream_t st) {
+  const double c1 = stage == 1 ? 0.5 * dt : dt, c2 = stage == 1 ? dt * dt / 8.0 : dt * dt / 6.0;
+  k_s2o4_stage<<<blocks_for(n, 256), 256, 0, st>>>(n, stage, c1, c2, Q, L, Lt, Lts, out);
+}
+void launch_s2o4_stage_vjp(int64_t n, int stage, double dt, const double* g, double* gQ,
+                           double* gL, double* gLt, double* gLts, cudaStream_t st) {
+  const double c1 = stage == 1 ? 0.5 * dt : dt, c2 = stage == 1 ? dt * dt / 8.0 : dt * dt / 6.0;
+  k_s2o4_stage_vjp<<<blocks_for(n, 256), 256, 0, st>>>(n, stage, c1, c2, g, gQ, gL, gLt, gLts);
+}
+
 template <class R>
 void launch_jacobi_init(const DevMesh& m, const R* fface, const R* fn, const double* vol,
                         double dt, const R* QA, R* Rv, R* D, R* hrs, R* dQ0,
@@ -1247,9 +1344,11 @@ template void launch_gather<double>(const DevMesh&, const Geo64&, const double*,
 template void launch_gather<float>(const DevMesh&, const Geo64&, const float*, double*, double*,
                                    cudaStream_t);
 template void launch_stage<double>(const DevMesh&, const GeoR<double>&, const double*, int, double,
-                                   void*, void*, double*, double*, int*, cudaStream_t);
+                                   void*, void*, double*, double*, int*, cudaStream_t, double*,
+                                   const double*);
 template void launch_stage<float>(const DevMesh&, const GeoR<float>&, const float*, int, double,
-                                  void*, void*, float*, float*, int*, cudaStream_t);
+                                  void*, void*, float*, float*, int*, cudaStream_t, double*,
+                                  const double*);
 template void launch_unpack<double>(int64_t, const double*, double*, cudaStream_t);
 template void launch_jacobi_init<double>(const DevMesh&, const double*, const double*,
                                          const double*, double, const double*, double*, double*,

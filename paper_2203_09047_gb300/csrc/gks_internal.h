@@ -88,6 +88,7 @@ void set_global_error(const char* msg);
 // Host mesh construction (gks_mesh.cpp). Returns a status and fills err.
 gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
                            const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
-                           const double lo[3], const double hi[3], HostMesh& m,
+                           const double lo[3], const double hi[3], int reorder, int min_stencil,
+                           HostMesh& m,
                            std::string& err);
 }  // namespace gks

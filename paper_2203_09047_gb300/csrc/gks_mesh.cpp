@@ -111,10 +111,18 @@ struct Nb {
 
 gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
                            const int8_t* cell_type, const int64_t* cell_nodes, const int bc[3],
-                           const double lo[3], const double hi[3], HostMesh& m,
-                           std::string& err) {
+                           const double lo[3], const double hi[3], int reorder, int min_stencil,
+                           HostMesh& m, std::string& err) {
   if (n_nodes <= 0 || n_cells <= 0 || !xyz || !cell_type || !cell_nodes || !bc || !lo || !hi) {
     err = "empty mesh or null array";
+    return GKS_E_INVAL;
+  }
+  if (reorder < GKS_REORDER_NONE || reorder > GKS_REORDER_RCM) {
+    err = "unknown cell reorder";
+    return GKS_E_INVAL;
+  }
+  if (min_stencil < 0 || min_stencil > kMaxStencil) {
+    err = "min_stencil out of range";
     return GKS_E_INVAL;
   }
   if (n_cells >= (int64_t)kCellMask) {
@@ -316,23 +324,70 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
     i = e;
   }
 
-  // 3. cell order: by cell kind, then Morton order of the vertex mean, so that 32-cell tiles
-  //    hold cells with (nearly) the same stencil sizes
+  // 3. cell order: by cell kind (so that 32-cell tiles hold cells with (nearly) the same
+  //    stencil sizes), then the Morton order of the vertex mean (default), the reverse
+  //    Cuthill-McKee order of the face graph, or the caller's order
   std::vector<int32_t> perm(nc), inv(nc);
   {
-    std::vector<std::tuple<int, uint64_t, int32_t>> code(nc);
-    for (int64_t c = 0; c < nc; ++c) {
-      double x[3] = {0, 0, 0};
-      for (int s = 0; s < 8; ++s)
-        for (int a = 0; a < 3; ++a) x[a] += node_x(cell_nodes[8 * c + s], a) / 8.0;
-      uint64_t k = 0;
-      for (int a = 0; a < 3; ++a) {
-        double u = (x[a] - lo[a]) / L[a];
-        u = std::min(std::max(u, 0.0), 1.0);
-        k |= spread21((uint64_t)(u * 2097151.0)) << a;
+    std::vector<uint64_t> key(nc);
+    if (reorder == GKS_REORDER_MORTON) {
+      for (int64_t c = 0; c < nc; ++c) {
+        double x[3] = {0, 0, 0};
+        for (int s = 0; s < 8; ++s)
+          for (int a = 0; a < 3; ++a) x[a] += node_x(cell_nodes[8 * c + s], a) / 8.0;
+        uint64_t k = 0;
+        for (int a = 0; a < 3; ++a) {
+          double u = (x[a] - lo[a]) / L[a];
+          u = std::min(std::max(u, 0.0), 1.0);
+          k |= spread21((uint64_t)(u * 2097151.0)) << a;
+        }
+        key[c] = k;
       }
-      code[c] = std::make_tuple((int)cell_type[c], k, (int32_t)c);
+    } else if (reorder == GKS_REORDER_RCM) {
+      // Cuthill-McKee: breadth-first from an unvisited cell of least degree, neighbours in
+      // increasing degree (ties by id); the reverse of the visit order is the key
+      auto degree = [&](int64_t c) {
+        int d = 0;
+        for (int p = 0; p < n_faces_of(cell_type[c]); ++p)
+          if (nbs[fptr[c] + p].xf.nw == 0) ++d;
+        return d;
+      };
+      std::vector<int32_t> by_deg(nc);
+      std::iota(by_deg.begin(), by_deg.end(), 0);
+      std::stable_sort(by_deg.begin(), by_deg.end(),
+                       [&](int32_t a, int32_t b) { return degree(a) < degree(b); });
+      std::vector<char> seen(nc, 0);
+      std::vector<int32_t> order;
+      order.reserve(nc);
+      std::vector<int32_t> next;
+      for (int32_t s : by_deg) {
+        if (seen[s]) continue;
+        seen[s] = 1;
+        size_t head = order.size();
+        order.push_back(s);
+        while (head < order.size()) {
+          const int32_t c = order[head++];
+          next.clear();
+          for (int p = 0; p < n_faces_of(cell_type[c]); ++p) {
+            const Nb& b = nbs[fptr[c] + p];
+            if (b.xf.nw == 0 && !seen[b.cell]) {
+              seen[b.cell] = 1;
+              next.push_back(b.cell);
+            }
+          }
+          std::stable_sort(next.begin(), next.end(), [&](int32_t a, int32_t b) {
+            const int da = degree(a), db = degree(b);
+            return da != db ? da < db : a < b;
+          });
+          order.insert(order.end(), next.begin(), next.end());
+        }
+      }
+      for (int64_t i = 0; i < nc; ++i) key[order[i]] = (uint64_t)(nc - 1 - i);
+    } else {
+      for (int64_t c = 0; c < nc; ++c) key[c] = (uint64_t)c;
     }
+    std::vector<std::tuple<int, uint64_t, int32_t>> code(nc);
+    for (int64_t c = 0; c < nc; ++c) code[c] = std::make_tuple((int)cell_type[c], key[c], (int32_t)c);
     std::sort(code.begin(), code.end());
     for (int64_t i = 0; i < nc; ++i) {
       perm[i] = std::get<2>(code[i]);
@@ -460,6 +515,24 @@ gks_status build_host_mesh(int64_t n_nodes, const double* xyz, int64_t n_cells,
       r2.clear();
       ring2(p, r2);
       for (const Nb& e : r2) find_or_add(e);
+    }
+    // optional third ring (a reading, not in the paper): a big stencil with fewer than
+    // min_stencil members takes the face neighbours of its members, member by member in
+    // stencil order and face by face in face-label order, until it has min_stencil members;
+    // images that cross more than two wall planes are skipped
+    if ((int)list.size() < min_stencil) {
+      const size_t n2 = list.size();
+      for (size_t k = 0; k < n2 && (int)list.size() < min_stencil; ++k) {
+        const Nb mk = list[k];
+        const int tk = cell_type[mk.cell];
+        for (int q = 0; q < n_faces_of(tk) && (int)list.size() < min_stencil; ++q) {
+          Nb e;
+          e.cell = nbs[fptr[mk.cell] + q].cell;
+          e.xf = xf_compose(mk.xf, nbs[fptr[mk.cell] + q].xf);
+          if (e.xf.nw > 2) continue;
+          find_or_add(e);
+        }
+      }
     }
     const SubRule* rules;
     const int M = sub_rules(t, &rules);

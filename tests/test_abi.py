@@ -56,6 +56,35 @@ def test_mesh_counts_match_oracle(lib, n, layers, bc):
     assert nst == int(info["K"].sum())
 
 
+@pytest.mark.parametrize("n,layers,bc", [(8, "hybrid8", (0, 0, 0)), (8, "hybrid8", (1, 1, 1)),
+                                         (4, "tet", (3, 1, 2))])
+@pytest.mark.parametrize("reorder", [0, 1, 2])
+def test_enlarged_stencils_match_oracle(lib, n, layers, bc, reorder):
+    """min_stencil = 18: both sides take the same third-ring members, for every cell order; the
+    stencils that already had 18 or more members are unchanged."""
+    m = I.layered_box_mesh(n, layers, bc=bc)
+    h = gks.gks_mesh_create(m["xyz"], m["cell_type"], m["cell_nodes"], m["bc"], m["lo"], m["hi"],
+                            reorder=reorder, min_stencil=18)
+    try:
+        nc, nf, nst = gks.gks_mesh_counts(h)
+    finally:
+        gks.gks_mesh_destroy(h)
+    K = oracle.Mesh(m, min_stencil=18).cell_info()["K"]
+    K0 = oracle.Mesh(m).cell_info()["K"]
+    assert nst == int(K.sum())
+    assert np.all(K >= np.minimum(18, K0)) and np.all(K[K0 >= 18] == K0[K0 >= 18])
+    assert K.min() >= 18 or layers == "tet"  # tetrahedra at walls may run out of candidates
+
+
+def test_mesh_options_rejected(lib):
+    m = I.layered_box_mesh(4, "hex")
+    for kw in (dict(reorder=3), dict(min_stencil=-1), dict(min_stencil=65)):
+        with pytest.raises(gks.GksError) as e:
+            gks.gks_mesh_create(m["xyz"], m["cell_type"], m["cell_nodes"], m["bc"], m["lo"],
+                                m["hi"], **kw)
+        assert e.value.status == gks.GKS_E_INVAL
+
+
 def test_mesh_errors(lib):
     m = I.layered_box_mesh(4, "hex")
     bad = dict(m)

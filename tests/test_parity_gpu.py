@@ -199,3 +199,95 @@ def test_host_buffers_through_abi():
     gks.gks_residual(S.h, Q, 0.01, L, Lt)
     Ld, Ltd = S.residual(Q, 0.01)
     assert np.array_equal(L, Ld.cpu().numpy()) and np.array_equal(Lt, Ltd.cpu().numpy())
+
+
+def test_step_mixed_fp64_update_mode():
+    """GKS_PREC_MIXED_FP64UPD: FP32 reconstruction and flux, FP64 face sums and FP64 update of an
+    FP64 state. Within the mixed step tolerance of the oracle, conservative to FP64 round-off,
+    and an implicit step in between hands its state on to the explicit steps."""
+    m, om = mesh_pair()
+    Q = om.advection_average()
+    p = CASES["smooth_zero"]
+    dt = om.max_dt(oracle.params_vec(**p), Q, 0.5)
+    S = gks.Solver(m, precision=gks.GKS_PREC_MIXED_FP64UPD, **p)
+    S.set_state(Q)
+    S.step(dt, 3)
+    Qo = om.step(oracle.params_vec(**p), Q, dt, 3)
+    Qg = S.get_state().cpu().numpy()
+    assert rel(Qg, Qo) < MIXED_TOL_STEP
+    vol = om.cell_info()["vol"]
+    for v in range(5):
+        assert abs(vol @ Qg[v] - vol @ Q[v]) <= 1e-14 * np.abs(vol @ np.abs(Q[v]))
+    # an implicit step (it updates the float-pair copy) followed directly by an explicit step
+    # must start the explicit step from the implicit step's result; R reads the state out in
+    # between, which refreshes the FP64 state on the host call
+    S.step_implicit(dt, 1, 3)
+    S.step(dt, 1)
+    R = gks.Solver(m, precision=gks.GKS_PREC_MIXED_FP64UPD, **p)
+    R.set_state(torch.from_numpy(Qg).cuda())
+    R.step_implicit(dt, 1, 3)
+    R.get_state()
+    R.step(dt, 1)
+    assert torch.equal(S.get_state(), R.get_state())
+
+
+def test_s2o4_stage_calls_match_oracle_and_transpose():
+    """gks_s2o4_stage against the oracle's two-stage combinations (Section 3.3), and
+    gks_s2o4_stage_vjp as its exact transpose (dot-product identity)."""
+    rng = np.random.default_rng(51)
+    n = 5 * 1000 + 7
+    Q, L, Lt, Lts = (rng.normal(size=n) for _ in range(4))
+    dt = 0.013
+    Qs_o, Qn_o = oracle.s2o4(Q, L, Lt, Lts, dt)
+    d = [torch.from_numpy(a).cuda() for a in (Q, L, Lt, Lts)]
+    out1, out2 = torch.empty_like(d[0]), torch.empty_like(d[0])
+    s = torch.cuda.current_stream().cuda_stream
+    gks.gks_s2o4_stage(1, dt, d[0], d[1], d[2], None, out1, s)
+    gks.gks_s2o4_stage(2, dt, d[0], d[1], d[2], d[3], out2, s)
+    assert rel(out1.cpu(), Qs_o) < 1e-15 and rel(out2.cpu(), Qn_o) < 1e-15
+    g = torch.from_numpy(rng.normal(size=n)).cuda()
+    for stage, out in ((1, out1), (2, out2)):
+        gs = [torch.empty_like(g) for _ in range(4)]
+        gks.gks_s2o4_stage_vjp(stage, dt, g, gs[0], gs[1], gs[2], gs[3] if stage == 2 else None, s)
+        lhs = float((g * out).sum())
+        rhs = sum(float((gs[k] * d[k]).sum()) for k in range(3 if stage == 1 else 4))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    with pytest.raises(gks.GksError):
+        gks.gks_s2o4_stage(3, dt, d[0], d[1], d[2], d[3], out1, s)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_enlarged_stencils_match_oracle(bc):
+    """min_stencil = 18 (the third-ring reading of gks_mesh_options) on the hybrid generator:
+    the GPU path and the oracle take the same members; FP64 at 1e-12, mixed at MIXED_TOL_L."""
+    lo, hi = ((0, 0, 0), (2, 2, 2)) if bc[0] == 0 else ((-1, -1, -1), (1, 1, 1))
+    m = I.layered_box_mesh(8, "hybrid8", lo=lo, hi=hi, bc=bc)
+    om = oracle.Mesh(m, min_stencil=18)
+    Q = I.perturbed_state(oracle.Mesh(m).advection_average() if bc[0] == 0 else
+                          np.tile(np.array([[0.8], [0.0], [0.0], [0.0], [1.1 / 0.4]]),
+                                  (1, om.n_cells)), seed=16, amp=0.02)
+    p = CASES["full_viscous"]
+    Lo, Lto = om.residual(oracle.params_vec(**p), Q, 0.01)
+    for prec, tol in ((gks.GKS_PREC_FP64, FP64_TOL), (gks.GKS_PREC_MIXED, MIXED_TOL_L)):
+        S = gks.Solver(m, min_stencil=18, precision=prec, **p)
+        L, Lt = S.residual(Q, 0.01)
+        assert rel(L.cpu(), Lo) < tol and rel(Lt.cpu(), Lto) < 10 * tol, (prec, rel(L.cpu(), Lo))
+        S.close()
+
+
+def test_cell_order_leaves_results_bitwise():
+    """Every cell's arithmetic runs in its own fixed face and stencil order, so the internal
+    cell order (caller order, Morton, reverse Cuthill-McKee) changes no bit of the results."""
+    m, om = mesh_pair()
+    Q = smooth_state(m, om, seed=17)
+    p = CASES["full_viscous"]
+    out = []
+    for reorder in (gks.GKS_REORDER_NONE, gks.GKS_REORDER_MORTON, gks.GKS_REORDER_RCM):
+        S = gks.Solver(m, reorder=reorder, **p)
+        L, Lt = S.residual(Q, 0.01)
+        S.set_state(Q)
+        S.step(0.004, 2)
+        out.append((L, Lt, S.get_state()))
+        S.close()
+    for k in (1, 2):
+        assert all(torch.equal(a, b) for a, b in zip(out[0], out[k]))
