@@ -37,7 +37,7 @@ typedef enum {
   GKS_E_MESH = 4,        /* non-conforming, inverted or unmatched cell/face */
   GKS_E_SINGULAR = 5,    /* a stencil least-squares system is rank deficient */
   GKS_E_NONPHYSICAL = 6, /* rho <= 0, p <= 0 or NaN in a state or a reconstructed value */
-  GKS_E_TIMEOUT = 7      /* reserved: a bounded device wait gave up */
+  GKS_E_TIMEOUT = 7      /* a bounded device wait gave up (reported by the status checks) */
 } gks_status;
 
 typedef struct gks_mesh gks_mesh;     /* opaque: topology, stencils, cell order */
@@ -209,6 +209,17 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps);
  * rho <= 0, p <= 0 or NaN (the device flag is then cleared). */
 gks_status gks_check(gks_solver* s);
 
+/* Test hook for the bounded wait of the reconstruction (the paper has no counterpart): every
+ * later reconstruction of this solver waits for its bulk copies (pseudo-inverse rows and
+ * sub-stencil entries staged into shared memory) at most wait_tries mbarrier tries per wait
+ * (0: the library default of 2^22), and with withhold_copies != 0 issues no copy at all, so the
+ * barrier never completes, every block gives up after its tries with nothing in flight, and
+ * the next status check (gks_check, gks_residual) returns GKS_E_TIMEOUT. The reconstruction's
+ * output is then undefined; gks_debug_recon_wait(s, 0, 0) restores normal operation. Meshes
+ * whose tile ranges all exceed the shared-memory limit of the copies have no such wait.
+ * Errors: GKS_E_INVAL (s NULL, wait_tries < 0). */
+gks_status gks_debug_recon_wait(gks_solver* s, int wait_tries, int withhold_copies);
+
 /* The two stage combinations of gks_step (Section 3.3) on caller arrays, for a rollout built
  * from gks_residual calls (a differentiable rollout, or a caller's own stepping):
  *   stage 1: out = Q + dt/2 L + dt^2/8 Lt              (Lts is not read; may be NULL)
@@ -322,6 +333,28 @@ gks_status gks_alu_peaks(double* fp32_tflops, double* fp64_tflops);
  * cudaDeviceReset between calls. Returns GKS_OK once both kernels are enqueued. */
 gks_status gks_cfl_dt_noalloc(int64_t n_cells, const double* Q, const double* h, double gamma,
                               double mu, double cfl, double* dt, void* stream);
+
+/* Domain decomposition for several ranks (one process per GPU; a plan, the caller moves the
+ * data). The paper runs one GPU. The cells are split into nranks contiguous ranges of the
+ * Morton order of their vertex means (the first n_cells % nranks ranks take one cell more). A
+ * rank's residual (Eq. finite) reads the reconstruction polynomials of its cells and of their
+ * face neighbours, and each polynomial its big stencil (Section 2), so the rank's halo is every
+ * other cell in {j} + stencil(j) for j in {i} + face neighbours(i), i owned (up to three face
+ * rings). A two-stage step exchanges the halo twice (Q^n and Q*), and the time step is the
+ * minimum over the ranks. Cell ids are the caller's. Errors: GKS_E_INVAL (nranks < 1, rank out
+ * of range, more ranks than cells), GKS_E_NOMEM. The mesh may be destroyed afterwards. */
+typedef struct gks_partition gks_partition;
+gks_status gks_partition_create(const gks_mesh* m, int nranks, int rank, gks_partition** out);
+/* Number of owned and halo cells of this rank. */
+gks_status gks_partition_counts(const gks_partition* p, int64_t* n_owned, int64_t* n_halo);
+/* Owned cells (Morton order), halo cells sorted by (owning rank, id) and their owning ranks;
+ * arrays of the counts' sizes, any may be NULL. */
+gks_status gks_partition_cells(const gks_partition* p, int64_t* owned, int64_t* halo,
+                               int32_t* halo_owner);
+/* The owned cells that rank `peer` holds in its halo, in that rank's halo order (cells = NULL:
+ * only *n); the peer receives them into its halo entries owned by this rank, in order. */
+gks_status gks_partition_send(const gks_partition* p, int peer, int64_t* n, int64_t* cells);
+void gks_partition_destroy(gks_partition* p);
 
 /* Text of the solver's last error (s = NULL: the last mesh-construction or stand-alone-call
  * error on this thread). */

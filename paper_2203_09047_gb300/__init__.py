@@ -109,6 +109,18 @@ def load_library(path: str = LIB_PATH):
     L.gks_cfl_dt_noalloc.argtypes = [I64, P, P, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, P, P]
     L.gks_cfl_dt_noalloc.restype = st
+    L.gks_partition_create.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
+    L.gks_partition_create.restype = st
+    L.gks_partition_counts.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.gks_partition_counts.restype = st
+    L.gks_partition_cells.argtypes = [P, P, P, P]
+    L.gks_partition_cells.restype = st
+    L.gks_partition_send.argtypes = [P, ctypes.c_int, ctypes.POINTER(I64), P]
+    L.gks_partition_send.restype = st
+    L.gks_partition_destroy.argtypes = [P]
+    L.gks_partition_destroy.restype = None
+    L.gks_debug_recon_wait.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    L.gks_debug_recon_wait.restype = st
     L.gks_alu_peaks.argtypes = [D, D]
     L.gks_alu_peaks.restype = st
     L.gks_s2o4_stage.argtypes = [I64, ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
@@ -288,6 +300,11 @@ def gks_cfl_dt_noalloc(n_cells: int, Q, h, gamma: float, mu: float, cfl: float, 
                              ctypes.c_void_p(stream))
     if s != GKS_OK:
         raise GksError(s, L.gks_last_error(None).decode())
+
+
+def gks_debug_recon_wait(solver, wait_tries: int, withhold_copies: bool):
+    _check(load_library().gks_debug_recon_wait(solver, int(wait_tries), 1 if withhold_copies else 0),
+           solver)
 
 
 def gks_alu_peaks():

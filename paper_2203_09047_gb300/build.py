@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgks.so")
 SOURCES = ["gks_mesh.cpp", "gks_geom.cu", "gks_hot.cu", "gks_api.cu", "gks_opcount.cu", "gks_noalloc.cu",
-           "gks_host_check.cu", "gks_adjoint.cu", "gks_peaks.cu"]
+           "gks_host_check.cu", "gks_adjoint.cu", "gks_peaks.cu", "gks_partition.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr"]

@@ -495,12 +495,13 @@ def couette(n=8, mu=0.05, mach=0.15, steps=3000, every=500, cfl=2.0, kmax=3, flu
     return rec
 
 
-def explosion(n=32, t_end=0.25, cfl=0.5, chunk=5, gp_fallback=1, precisions=("fp64", "mixed"),
+def explosion(n=32, t_end=0.25, cfl=0.5, chunk=1, gp_fallback=1, precisions=("fp64", "mixed"),
               min_stencil=18):
     """Spherical explosion in the reflecting box [-1,1]^3 on the hybrid generator (full flux,
     inviscid collision time, WENO nonlinear weights): inside r < 0.4 rho = p = 1, outside
-    rho = 0.125, p = 0.1, at rest. The FP64 run takes dt = CFL-bounded every `chunk` steps and the
-    mixed run replays the same dt sequence. Reports per precision: steps, cell-stage updates/s of
+    rho = 0.125, p = 0.1, at rest. The FP64 run takes the CFL-bounded dt every `chunk` steps (1:
+    every step; the blast accelerates the gas from rest, so a dt held for several steps from the
+    early state exceeds the bound) and the mixed run replays the same dt sequence. Reports per precision: steps, cell-stage updates/s of
     the stepping, relative mass and energy drift (total and per step), min rho and p; and the
     mixed-vs-FP64 density difference (volume-weighted L1 per unit volume, relative to the mean
     density). gp_fallback = 1 takes the first-order state at Gauss points whose reconstruction is

@@ -43,6 +43,8 @@ struct gks_solver {
   GeoR<float> gf;
   bool mixed = false;
   bool fp64upd = false;     // GKS_PREC_MIXED_FP64UPD: Q (FP64) is the master state of the steps
+  int dbg_wait_tries = 0;   // gks_debug_recon_wait
+  int dbg_withhold = 0;
   // buffers (internal order)
   // The state lives in the gather copy QA (FP64 values, or float-float pairs on the FP32 path);
   // Q is its FP64 [5][nc] form, refreshed from QA when a call needs it (q_stale after steps).
@@ -205,7 +207,9 @@ void precompute_r(gks_solver* s, GeoR<R>& g) {
 template <class R>
 void residual_r(gks_solver* s, GeoR<R>& g, const void* QinA, double dt, int mode, double* L,
                 double* Lt) {
-  const KParams<R> kp = kparams<R>(s->prm);
+  KParams<R> kp = kparams<R>(s->prm);
+  kp.wait_tries = s->dbg_wait_tries;
+  kp.withhold = s->dbg_withhold;
   int t = s->tick(0);
   launch_recon<R>(s->m, g, kp, (const R*)QinA, (R*)s->poly, s->flag, s->st, &s->fj);
   s->tock(t);
@@ -433,7 +437,9 @@ gks_status step_implicit_r(gks_solver* s, GeoR<R>& g, double dt, int nsteps, int
     launch_face_normals<R>(s->m, fn, s->st);
     s->imp_ready = true;
   }
-  const KParams<R> kp = kparams<R>(s->prm);
+  KParams<R> kp = kparams<R>(s->prm);
+  kp.wait_tries = s->dbg_wait_tries;
+  kp.withhold = s->dbg_withhold;
   R* dq[2] = {(R*)s->jdQ[0], (R*)s->jdQ[1]};
   for (int n = 0; n < nsteps; ++n) {
     int t = s->tick(0);
@@ -762,6 +768,13 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps) {
   if (nsteps > 0 && !s->fp64upd) s->q_stale = true;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GKS_OK : s->cuda_fail(e, "step launch");
+}
+
+gks_status gks_debug_recon_wait(gks_solver* s, int wait_tries, int withhold_copies) {
+  if (!s || wait_tries < 0) return GKS_E_INVAL;
+  s->dbg_wait_tries = wait_tries;
+  s->dbg_withhold = withhold_copies != 0;
+  return GKS_OK;
 }
 
 gks_status gks_s2o4_stage(int64_t n, int stage, double dt, const double* Q, const double* L,

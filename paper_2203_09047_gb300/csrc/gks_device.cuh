@@ -139,6 +139,10 @@ struct KParams {
   int weno_pow;
   R T_ref, mu_pow;  // power-law viscosity (the boundary planes live in DevMesh::wall64/wall32)
   int gp_fallback;  // first-order state at Gauss points whose reconstruction is non-physical
+  // test hook (gks_debug_recon_wait): bounded-wait limit of the reconstruction's bulk copies
+  // (0: the default) and whether the copies are withheld
+  int wait_tries = 0;
+  int withhold = 0;
 };
 
 // ---- precompute (gks_geom.cu) -------------------------------------------------------------

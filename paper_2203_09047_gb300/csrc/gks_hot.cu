@@ -132,10 +132,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Each try_wait suspends the thread for at most a hardware time limit; the loop gives up after
-// kWaitTries attempts (far beyond the microseconds a tile's copies take).
+// `tries` attempts (by default kWaitTries, far beyond the microseconds a tile's copies take).
 constexpr int kWaitTries = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitTries; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tries) {
+  for (int it = 0; it < tries; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
     const int32_t* __restrict__ t_st, const int32_t* __restrict__ t_sb,
     const int32_t* __restrict__ t_idx, const int8_t* __restrict__ n_sub,
     const R* __restrict__ Ap, const R* __restrict__ Bp, const R* __restrict__ mom,
-    const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly, int* flag) {
+    const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly, int* flag,
+    int wait_tries, int withhold) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ReconSmem<R> L(Kr, Sr, Mr, kPf);
   R* sa = reinterpret_cast<R*>(smem_raw + L.ca_off);      // [n][v][lane]
@@ -223,8 +224,13 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
       const uint32_t ab = 9u * K * kTile * sizeof(R),
                      bb = bulk_b<R>() ? 4u * S * kTile * sizeof(R) : 0u;
       mbar_expect_tx(bar, ab + bb);
-      bulk_load(smem_raw + L.a_off, Ag, ab, bar);
-      if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
+      // withhold != 0 (the timeout test of gks_debug_recon_wait): no copy is issued, so the
+      // barrier's phase never completes and the bounded wait below runs out with nothing in
+      // flight
+      if (!withhold) {
+        bulk_load(smem_raw + L.a_off, Ag, ab, bar);
+        if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
+      }
     }
   }
   const int64_t i = tile * kTile + lane;
@@ -270,8 +276,9 @@ __global__ void __launch_bounds__(kReconThreads) k_recon(
   const R* Bt;
   if (kPf) {
     // every thread waits for the copies; a block whose wait ran out reports it and stops
-    bool ok = mbar_wait(bar, 0);
-    if (!ok) ok = mbar_wait(bar, 0);  // let copies still in flight land before leaving
+    const int tries = wait_tries > 0 ? wait_tries : kWaitTries;
+    bool ok = mbar_wait(bar, 0, tries);
+    if (!ok) ok = mbar_wait(bar, 0, tries);  // let copies still in flight land before leaving
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) atomicOr(flag, kErrTimeout);
       return;
@@ -1091,7 +1098,8 @@ void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p,
     cudaFuncSetAttribute(k_recon<R, kPf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_recon<R, kPf><<<(unsigned)(m.rr.t1[r] - m.rr.t0[r]), kReconThreads, smem, st>>>(
       m.nc, m.rr.t0[r], m.rr.K[r], m.rr.S[r], m.rr.M[r], QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
-      m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag);
+      m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag,
+      p.wait_tries, p.withhold);
 }
 
 // Ghost slots of moving no-slip walls and far-field planes: QA[nc + g] = the image's flow

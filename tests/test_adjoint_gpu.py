@@ -129,3 +129,81 @@ def test_checkpointed_s2o4_rollout_gradient():
     QTo, dQTo = om.step_jvp(oracle.params_vec(**p), Q0, d, dt, nsteps)
     jd = (2.0 * om.cell_info()["vol"] * QTo[0] * dQTo[0]).sum()
     assert abs((grad * d).sum() - jd) <= 1e-9 * abs(jd)
+
+
+def _jacobian_columns(om, params, Q, dt, cols):
+    """Columns of d(L, Lt)/dQ for the (variable, cell) pairs in cols, from the oracle's
+    dual-number JVP: [len(cols)][2][5][n]."""
+    out = []
+    for v, c in cols:
+        dQ = np.zeros_like(Q)
+        dQ[v, c] = 1.0
+        _, _, dL, dLt = om.residual_jvp(params, Q, dQ, dt)
+        out.append(np.stack([dL, dLt]))
+    return np.array(out)
+
+
+def _vjp_rows(S, Q, dt, rows, n):
+    """Rows of d(L, Lt)/dQ for the (output, variable, cell) triples in rows (output 0: L,
+    1: Lt), from the GPU VJP with a unit cotangent: [len(rows)][5][n]."""
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    g0 = torch.zeros((5, n), dtype=torch.float64, device="cuda")
+    gQ = torch.empty_like(Qd)
+    out = []
+    for o, w, j in rows:
+        gL, gLt = g0.clone(), g0.clone()
+        (gL if o == 0 else gLt)[w, j] = 1.0
+        gks.gks_residual_vjp(S.h, Qd, dt, gL, gLt, gQ)
+        out.append(gQ.cpu().numpy())
+    return np.array(out)
+
+
+@pytest.mark.parametrize("case", ["full_viscous", "smooth_zero"])
+def test_vjp_full_jacobian_elementwise_small_hex_mesh(case):
+    """Every entry of the transposed Jacobian from the GPU VJP (one unit cotangent per row)
+    against every column of the oracle's dual-number JVP, on 4^3 periodic hexahedra (64 cells,
+    a 640 x 320 matrix), nonlinear weights active on a perturbed state."""
+    m, om = mesh_pair(4, "hex")
+    n = om.n_cells
+    Q = I.perturbed_state(om.advection_average(), seed=71, amp=0.03)
+    p = CASES[case]
+    dt = 0.01
+    J = _jacobian_columns(om, oracle.params_vec(**p), Q, dt,
+                          [(v, c) for v in range(5) for c in range(n)])  # [(v,c)][o][w][j]
+    S = gks.Solver(m, **p)
+    rows = [(o, w, j) for o in range(2) for w in range(5) for j in range(n)]
+    G = _vjp_rows(S, Q, dt, rows, n)  # [(o,w,j)][v][c]
+    Jt = J.reshape(5 * n, 2 * 5 * n).T  # [(o,w,j)][(v,c)]
+    Gm = G.reshape(2 * 5 * n, 5 * n)
+    scale = np.abs(Jt).max()
+    assert np.abs(Gm - Jt).max() <= 1e-10 * scale, np.abs(Gm - Jt).max() / scale
+    S.close()
+
+
+def test_vjp_jacobian_columns_elementwise_hybrid_mesh():
+    """Entries of three full columns of the Jacobian (a split-pyramid tetrahedron, a pyramid and
+    a prism of the 8^3 hybrid box with enlarged stencils, every variable) from GPU VJP rows over
+    the columns' support, against the oracle's JVP columns; rows outside the support read 0."""
+    m = I.layered_box_mesh(8, "hybrid8")
+    om = oracle.Mesh(m, min_stencil=18)
+    n = om.n_cells
+    Q = I.perturbed_state(oracle.Mesh(m).advection_average(), seed=72, amp=0.03)
+    p = CASES["full_viscous"]
+    dt = 0.01
+    types = m["cell_type"]
+    cells = [int(np.nonzero(types == t)[0][len(np.nonzero(types == t)[0]) // 2]) for t in (4, 5, 6)]
+    cols = [(v, c) for c in cells for v in range(5)]
+    J = _jacobian_columns(om, oracle.params_vec(**p), Q, dt, cols)  # [col][o][w][j]
+    support = np.nonzero(np.abs(J).max(axis=(0, 1, 2)) > 0)[0]
+    outside = np.setdiff1d(np.arange(n), support)[:8]
+    S = gks.Solver(m, min_stencil=18, **p)
+    rows = [(o, w, j) for j in np.concatenate([support, outside]) for o in range(2)
+            for w in range(5)]
+    G = _vjp_rows(S, Q, dt, rows, n)
+    scale = np.abs(J).max()
+    worst = 0.0
+    for r, (o, w, j) in enumerate(rows):
+        for k, (v, c) in enumerate(cols):
+            worst = max(worst, abs(G[r, v, c] - J[k, o, w, j]))
+    assert worst <= 1e-10 * scale, worst / scale
+    S.close()
