@@ -517,7 +517,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_desc(args.n, nc, nf),
+        "config": workload_desc(args.n, nc, nf, min_stencil=args.min_stencil),
         "clocks": mixed["clocks"],
         "gpu_launches": int(sum(c * l for c, l in zip(mixed["kcnt"], gks.gks_launches_per_pass(S.h)))),
         "roofline": roof_for(kt, True),

@@ -99,8 +99,7 @@ typedef struct {
    * invariant u_n + 2c/(gamma-1) from inside, the incoming u_n - 2c/(gamma-1) from this state,
    * entropy and tangential velocity from the upwind side (supersonic inflow: this state,
    * supersonic outflow: the inside state); it carries no gradient at the Gauss points. One state
-   * per plane (axis + 3 side), default (1, 0, 0, 0, 1/1.4). gks_residual_vjp rejects meshes
-   * with far-field planes (GKS_E_INVAL). */
+   * per plane (axis + 3 side), default (1, 0, 0, 0, 1/1.4). */
   double farfield[6][5];
   /* Positivity fallback at the Gauss points (not in the paper, which prints no positivity
    * treatment; off by default): with gp_fallback != 0, a side whose reconstructed state at a face

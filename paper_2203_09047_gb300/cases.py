@@ -145,17 +145,18 @@ def tgv(n=48, steps=200, cfl=0.5, re=1600.0, mach=0.1, pr=0.72):
     return rec
 
 
-def adjoint(n=32, steps=200, every=20, ndirs=20, mu=1e-3, cfl=0.5, eps=1e-6, layers="tet"):
+def adjoint(n=32, steps=200, every=20, ndirs=20, mu=1e-3, cfl=0.5, eps=1e-6, layers="hybrid8",
+            min_stencil=18):
     """Gradient of J = sum |Omega| rho^2 at the final time with respect to the initial state,
     through `steps` S2O4 steps with checkpoints every `every`, against central differences on
-    `ndirs` random directions (Navier-Stokes, full flux, viscous collision time). The default
-    mesh is the Kuhn-tetrahedron box; on the hybrid generator the transition layers' nearly
-    singular pyramid stencils make J non-smooth over 200 steps (central differences do not
-    converge there)."""
+    `ndirs` random directions (Navier-Stokes, full flux, viscous collision time), on the C4 mesh:
+    the hybrid generator at 32 cubes with the enlarged stencils (min_stencil 18). With the
+    stencils as printed (min_stencil 0) the transition layers' unstable reconstruction makes J
+    non-smooth over 200 steps and central differences do not converge."""
     import torch
     from .autograd import s2o4_rollout
     m = I.layered_box_mesh(n, layers)
-    S = Solver(m, flux_mode=1, tau_model=2, mu=mu)
+    S = Solver(m, flux_mode=1, tau_model=2, mu=mu, min_stencil=min_stencil)
     Qc = S.cell_average(_exact_advection(0.0))
     Q0 = I.perturbed_state(Qc, seed=2, amp=0.01)
     S.set_state(Q0)
@@ -179,8 +180,8 @@ def adjoint(n=32, steps=200, every=20, ndirs=20, mu=1e-3, cfl=0.5, eps=1e-6, lay
             fd = (J(Qt + eps * dd) - J(Qt - eps * dd)).item() / (2 * eps)
             ad = float((grad * dd).sum())
             worst = max(worst, abs(ad - fd) / abs(fd))
-    rec = {"case": "adjoint", "mesh": layers, "cubes": n, "cells": S.n_cells, "steps": steps,
-           "checkpoint_every": every,
+    rec = {"case": "adjoint", "mesh": layers, "min_stencil": min_stencil, "cubes": n,
+           "cells": S.n_cells, "steps": steps, "checkpoint_every": every,
            "directions": ndirs, "fd_eps": eps, "max_rel_diff_vs_fd": worst, "gradient_wall_s": t_grad}
     _emit(rec)
     return rec

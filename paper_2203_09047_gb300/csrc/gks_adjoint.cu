@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(128) k_vjp_flux(
         poly_mean(poly + (int64_t)kPolyStride * nb, mun, vr, gr);
       }
     } else {
-      wall_ghost<double, false>(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
+      wall_ghost<double, true>(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);
     }
     double gvl[5] = {0, 0, 0, 0, 0}, gvr[5] = {0, 0, 0, 0, 0};
     double ggl[5][3], ggr[5][3];

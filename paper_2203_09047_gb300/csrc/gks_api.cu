@@ -846,9 +846,6 @@ gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const dou
                             const double* gLt, double* gQ) {
   if (!s || !Q || !gL || !gLt || !gQ || !(dt > 0)) return GKS_E_INVAL;
   if (s->prm.Pr != 1.0) return s->fail(GKS_E_INVAL, "the VJP supports Pr = 1 only");
-  for (int a = 0; a < 3; ++a)
-    if (((s->m.bcs >> (2 * a)) & 3) == GKS_BC_FARFIELD)
-      return s->fail(GKS_E_INVAL, "the VJP does not take far-field planes");
   const int64_t nc = s->m.nc, nf = s->m.nf;
   cudaError_t e = cudaSuccess;
   if (!s->vjp_ready) {

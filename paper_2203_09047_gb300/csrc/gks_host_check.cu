@@ -63,7 +63,7 @@ extern "C" int gks_gp_flux_vjp_host(const double* p, const double* ql, const dou
       ga[d][v] = gb[d][v] = 0.0;
     }
   for (int v = 0; v < 5; ++v) gql[v] = gqr[v] = 0.0;
-  if (!gks::gks_gp_flux_vjp(P, ql, a, qr, b, dt, gFn, gFt, gql, ga, gqr, gb)) return 1;
+  if (!gks::gks_gp_flux_vjp_cf(P, ql, a, qr, b, dt, gFn, gFt, gql, ga, gqr, gb)) return 1;
   for (int d = 0; d < 3; ++d)
     for (int v = 0; v < 5; ++v) {
       gdql[5 * d + v] = ga[d][v];

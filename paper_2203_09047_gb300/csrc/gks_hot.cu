@@ -187,8 +187,12 @@ struct ReconSmem {
   }
 };
 
+// Five resident blocks per SM as the register bound (at most 80 registers a thread): on the
+// 64^3-cube hybrid mesh with the enlarged stencils 0.664 ms per FP32 pass against 0.697 ms
+// unbounded (82 registers, 4 blocks), 0.786 ms at 6 blocks (64 registers); the ranges whose
+// shared memory allows fewer blocks are unaffected.
 template <class R, bool kPf>
-__global__ void __launch_bounds__(kReconThreads) k_recon(
+__global__ void __launch_bounds__(kReconThreads, 5) k_recon(
     int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, const R* __restrict__ QA,
     const int32_t* __restrict__ t_K, const uint64_t* __restrict__ t_cnt,
     const int32_t* __restrict__ t_st, const int32_t* __restrict__ t_sb,

@@ -1,5 +1,6 @@
-// Gas-kinetic flux at one Gauss point (Section 3.2), written for the GPU: closed-form
-// Maxwellian moments, closed-form slope solves, and the time-fitted flux F^n, dF/dt.
+// Gas-kinetic flux at one Gauss point (Section 3.2), written for the GPU: the half-space and
+// interface-equilibrium moments in closed form, the slope terms as directional derivatives of
+// closed-form moment vectors (no slope solve), and the time-fitted flux F^n, dF/dt.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,116 +23,6 @@ GKS_HD double k_abs(double x) { return fabs(x); }
 GKS_HD float k_abs(float x) { return fabsf(x); }
 GKS_HD double k_pow(double x, double y) { return pow(x, y); }
 GKS_HD float k_pow(float x, float y) { return powf(x, y); }
-
-// Moments <u^k>, <v^l>, <w^m>, <xi^(2x)> of a unit-density Maxwellian (u possibly over a
-// half line).
-template <class R>
-struct Mom {
-  R u[7], v[6], w[6], xi[3];
-};
-
-// Full-line moments by the Gaussian recurrence <c^(n+1)> = C <c^n> + n/(2 lambda) <c^(n-1)>.
-template <class R, int N>
-GKS_HD void line_moments(R c, R half_inv_lam, R* out) {
-  out[0] = R(1);
-  out[1] = c;
-#pragma unroll
-  for (int n = 2; n < N; ++n) out[n] = c * out[n - 1] + R(n - 1) * half_inv_lam * out[n - 2];
-}
-
-// Moments of a Maxwellian with velocity (U,V,W) and lambda = rho/(2p). side = 0: full line in u,
-// +1: u > 0, -1: u < 0.
-template <class R>
-GKS_HD void maxwell_moments(R U, R V, R W, R lam, R K, int side, Mom<R>& M) {
-  const R hil = R(0.5) / lam;
-  line_moments<R, 6>(V, hil, M.v);
-  line_moments<R, 6>(W, hil, M.w);
-  if (side == 0) {
-    line_moments<R, 7>(U, hil, M.u);
-  } else {
-    const R sl = k_sqrt(lam);
-    const R s = R(side);
-    M.u[0] = R(0.5) * k_erfc(-s * sl * U);
-    M.u[1] = U * M.u[0] + s * R(0.28209479177387814) * k_exp(-lam * U * U) / sl;  // 1/(2 sqrt(pi))
-#pragma unroll
-    for (int n = 2; n < 7; ++n) M.u[n] = U * M.u[n - 1] + R(n - 1) * hil * M.u[n - 2];
-  }
-  M.xi[0] = R(1);
-  M.xi[1] = K * hil;
-  M.xi[2] = K * (K + R(2)) * hil * hil;
-}
-
-// <u^k v^l w^m xi^(2x) psi>, psi = (1, u, v, w, (u^2+v^2+w^2+xi^2)/2).
-template <class R>
-GKS_HD void G(const Mom<R>& M, int k, int l, int m, int x, R o[5]) {
-  const R b = M.v[l] * M.w[m] * M.xi[x];
-  o[0] = M.u[k] * b;
-  o[1] = M.u[k + 1] * b;
-  o[2] = M.u[k] * M.v[l + 1] * M.w[m] * M.xi[x];
-  o[3] = M.u[k] * M.v[l] * M.w[m + 1] * M.xi[x];
-  o[4] = R(0.5) * (M.u[k + 2] * b + M.u[k] * M.v[l + 2] * M.w[m] * M.xi[x] +
-                   M.u[k] * M.v[l] * M.w[m + 2] * M.xi[x] + M.u[k] * M.v[l] * M.w[m] * M.xi[x + 1]);
-}
-
-// <a u^k v^l w^m psi> with a = a0 + a1 u + a2 v + a3 w + a4 (u^2+v^2+w^2+xi^2)/2.
-template <class R>
-GKS_HD void Ga(const Mom<R>& M, const R a[5], int k, int l, int m, R o[5]) {
-  R t[5];
-  G(M, k, l, m, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] = a[0] * t[q];
-  G(M, k + 1, l, m, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += a[1] * t[q];
-  G(M, k, l + 1, m, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += a[2] * t[q];
-  G(M, k, l, m + 1, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += a[3] * t[q];
-  const R h4 = R(0.5) * a[4];
-  G(M, k + 2, l, m, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
-  G(M, k, l + 2, m, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
-  G(M, k, l, m + 2, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
-  G(M, k, l, m, 1, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += h4 * t[q];
-}
-
-// <u^k (a1 u + a2 v + a3 w) psi> for three slope polynomials a1, a2, a3.
-template <class R>
-GKS_HD void Gadotu(const Mom<R>& M, const R a[3][5], int k, R o[5]) {
-  R t[5];
-  Ga(M, a[0], k + 1, 0, 0, o);
-  Ga(M, a[1], k, 1, 0, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += t[q];
-  Ga(M, a[2], k, 0, 1, t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) o[q] += t[q];
-}
-
-// Solve <a psi> = b for the slope polynomial a of a Maxwellian (closed form of the 5x5 moment
-// system; b is the conserved-variable derivative divided by rho).
-template <class R>
-GKS_HD void slope_solve(R U, R V, R W, R lam, R K, const R b[5], R a[5]) {
-  const R q2 = U * U + V * V + W * W;
-  const R e2 = q2 + (K + R(3)) * R(0.5) / lam;
-  const R r1 = b[1] - U * b[0], r2 = b[2] - V * b[0], r3 = b[3] - W * b[0];
-  const R r4 = R(2) * b[4] - e2 * b[0];
-  a[4] = R(4) * lam * lam / (K + R(3)) * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
-  const R tl = R(2) * lam;
-  a[1] = tl * r1 - U * a[4];
-  a[2] = tl * r2 - V * a[4];
-  a[3] = tl * r3 - W * a[4];
-  a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * e2;
-}
 
 template <class R>
 struct Prim {

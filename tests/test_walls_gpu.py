@@ -226,15 +226,21 @@ def test_farfield_steps_and_implicit_match_oracle():
     assert rel(S.get_state().cpu(), om.step_implicit(P, Q, 4 * dt, 2, 3)) < FP64_TOL
 
 
-def test_farfield_vjp_is_rejected():
-    """gks_residual_vjp does not take far-field planes: it returns GKS_E_INVAL."""
-    m, om = mesh_pair(8, "hybrid8", (3, 3, 3))
+@pytest.mark.parametrize("bc", [(3, 3, 3), (3, 1, 2)])
+def test_farfield_vjp_dot_product_with_oracle_jvp(bc):
+    """The VJP through far-field planes (the characteristic map at the Gauss points and in the
+    stencil ghosts, reversed) against the oracle's dual-number directional derivative."""
+    m, om = mesh_pair(8, "hybrid8", bc)
+    uw = np.zeros((6, 3))
+    uw[5] = (0.1, -0.05, 0.0)
+    p = dict(flux_mode=1, tau_model=2, mu=2e-3)
     Q = farfield_state(om, seed=63)
-    gL, gLt, _ = I.normal_directions(Q.shape, 3, 64)
-    S = gks.Solver(m, farfield=FINF, flux_mode=1, tau_model=2, mu=2e-3)
-    with pytest.raises(gks.GksError) as e:
-        S.residual_vjp(Q, 0.004, gL, gLt)
-    assert e.value.status == gks.GKS_E_INVAL
+    gL, gLt, dQ = I.normal_directions(Q.shape, 3, 64)
+    S = gks.Solver(m, farfield=FINF, wall_u=uw, **p)
+    gQ = S.residual_vjp(Q, 0.004, gL, gLt).cpu().numpy()
+    _, _, dL, dLt = om.residual_jvp(oracle.params_vec(farfield=FINF, wall_u=uw, **p), Q, dQ, 0.004)
+    lhs, rhs = (gQ * dQ).sum(), (gL * dL).sum() + (gLt * dLt).sum()
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs), (lhs, rhs)
 
 
 @pytest.mark.parametrize("finf", [FINF, (1.0, 1.6, 0.3, -0.2, 1.0 / 1.4)])
