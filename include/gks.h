@@ -265,8 +265,11 @@ gks_status gks_residual(gks_solver* s, const double* Q, double dt, double* L, do
  * and nonlinear weights of Section 2, the derivative of |x| taken as sign(x) with +1 at 0), in
  * FP64 regardless of the solver's precision; deterministic (per-face and per-cell writes,
  * reverse-stencil gathers, no atomics). The first call allocates the adjoint buffers (and, for
- * a mixed-precision solver, an FP64 copy of the geometry). Synchronises the stream; returns
- * GKS_E_NONPHYSICAL for a non-physical state. */
+ * a mixed-precision solver, an FP64 copy of the geometry). The flux adjoint keeps up to 1.7 KB
+ * of stack per thread: when the context's per-thread stack limit (cudaLimitStackSize) is
+ * smaller, the call raises it, which reserves local memory for every resident thread of the
+ * context for as long as the context lives and may synchronise the device. Synchronises the
+ * stream; returns GKS_E_NONPHYSICAL for a non-physical state. */
 gks_status gks_residual_vjp(gks_solver* s, const double* Q, double dt, const double* gL,
                             const double* gLt, double* gQ);
 
