@@ -488,10 +488,11 @@ def run_gpu(args):
     for k, name in enumerate(["recon", "flux", "gather"]):
         kt64[name]["gbs"] = bytes64[k] / (kt64[name]["avg_ms"] * 1e-3) / 1e9
 
-    # DRAM bytes (read + write) per pass from the ncu captures of the FP32 kernels on the
-    # 48^3-cube mesh (profiles/k_recon_float_advection48_ncu.md,
-    # profiles/k_flux_float_smooth_advection48_ncu.md), scaled by cells or faces
-    dram_per_unit = {"recon": (1435.8, nc), "flux": (322.4, nf)}
+    # DRAM bytes (read + write) per pass of the FP32 reconstruction from the ncu capture on the
+    # 48^3-cube mesh with the enlarged stencils (profiles/k_recon_float_advection48_ncu.md),
+    # scaled by cells (same layer pattern and stencils); the flux kernel has changed since its
+    # capture, so it reports no traffic
+    dram_per_unit = {"recon": (1569.7, nc)}
 
     def roof_for(table, is_mixed):
         dom = max(table, key=lambda k: table[k]["share"] or 0)

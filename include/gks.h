@@ -209,13 +209,13 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps);
 gks_status gks_check(gks_solver* s);
 
 /* Test hook for the bounded wait of the reconstruction (the paper has no counterpart): every
- * later reconstruction of this solver waits for its bulk copies (pseudo-inverse rows and
- * sub-stencil entries staged into shared memory) at most wait_tries mbarrier tries per wait
- * (0: the library default of 2^22), and with withhold_copies != 0 issues no copy at all, so the
- * barrier never completes, every block gives up after its tries with nothing in flight, and
- * the next status check (gks_check, gks_residual) returns GKS_E_TIMEOUT. The reconstruction's
- * output is then undefined; gks_debug_recon_wait(s, 0, 0) restores normal operation. Meshes
- * whose tile ranges all exceed the shared-memory limit of the copies have no such wait.
+ * later reconstruction of this solver waits for its bulk copy (the FP32 sub-stencil entries
+ * staged into shared memory) at most wait_tries mbarrier tries per wait (0: the library default
+ * of 2^22), and with withhold_copies != 0 issues no copy at all, so the barrier never
+ * completes, every block gives up after its tries with nothing in flight, and the next status
+ * check (gks_check, gks_residual) returns GKS_E_TIMEOUT. The reconstruction's output is then
+ * undefined; gks_debug_recon_wait(s, 0, 0) restores normal operation. Only the mixed-precision
+ * modes stage that copy; the FP64 path reads the entries from global memory and has no wait.
  * Errors: GKS_E_INVAL (s NULL, wait_tries < 0). */
 gks_status gks_debug_recon_wait(gks_solver* s, int wait_tries, int withhold_copies);
 

@@ -150,10 +150,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tr
 //   beta_0, tau, omega, omega-bar (Section 2), one variable per warp               (phase 3)
 //   C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m, i.e. Eq. weno as one polynomial (phase 4)
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
-// With kPf the tile's pseudo-inverse rows and (FP32) sub-stencil entries, contiguous blocks of
-// the interleaved layouts, are brought into shared memory by bulk copies issued when the block
-// starts, so that their transfer overlaps phase 1; otherwise phase 2 reads them from global
-// memory.
+// With kPf, when the block starts, the tile's pseudo-inverse rows (a contiguous block of the
+// interleaved layout) are prefetched into L2 by a bulk prefetch and the FP32 sub-stencil entries
+// are copied into shared memory by a bulk copy on an mbarrier, so that both transfers overlap
+// phase 1; phase 2 then reads the rows from L2 (each row once, two rows per warp in one member
+// loop, so that two independent loads per member are in flight) and the entries from shared
+// memory. Without kPf phase 2 reads both from global memory. Staging the rows in shared memory
+// as well (they are read once, so the staging bought only the overlap) held the range's blocks
+// to 2-3 per SM: 0.669 against 0.598 ms per FP32 pass on the 64^3-cube mesh with the enlarged
+// stencils, 6.54 against 5.38 ms in FP64.
 constexpr int kReconWarps = 5;
 constexpr int kReconThreads = kReconWarps * kTile;
 
@@ -168,9 +173,9 @@ __host__ __device__ constexpr bool bulk_b() {
 
 // Shared-memory layout of one block for a range with largest stencil Kr, largest sum of
 // sub-stencil member counts Sr and largest number of sub-stencil slots Mr, in units of one
-// interleaved row (kTile values): [mbarrier, 16 B][A+ rows 9 Kr][B entries 4 Sr] (only with
-// kPf; B only when bulk_b), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part
-// starts on a 16-byte boundary.
+// interleaved row (kTile values): [mbarrier, 16 B][B entries 4 Sr] (only with kPf and when
+// bulk_b), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part starts on a 16-byte
+// boundary. (a_off marks where staged rows would start; the rows come through L2.)
 
 template <class R>
 struct ReconSmem {
@@ -178,7 +183,7 @@ struct ReconSmem {
   __host__ __device__ ReconSmem(int Kr, int Sr, int Mr, bool pf) {
     const size_t row = (size_t)kTile * sizeof(R);
     a_off = pf ? 16 : 0;
-    b_off = a_off + (pf ? 9 * (size_t)Kr * row : 0);
+    b_off = a_off;
     ca_off = b_off + (pf && bulk_b<R>() ? 4 * (size_t)Sr * row : 0);
     cb_off = ca_off + 45 * row;
     cbet_off = cb_off + 15 * (size_t)Mr * row;
@@ -187,10 +192,10 @@ struct ReconSmem {
   }
 };
 
-// Five resident blocks per SM as the register bound (at most 80 registers a thread): on the
-// 64^3-cube hybrid mesh with the enlarged stencils 0.664 ms per FP32 pass against 0.697 ms
-// unbounded (82 registers, 4 blocks), 0.786 ms at 6 blocks (64 registers); the ranges whose
-// shared memory allows fewer blocks are unaffected.
+// Five resident blocks per SM as the register bound (at most 80 registers a thread; 72 used):
+// on the 64^3-cube hybrid mesh with the enlarged stencils 0.598 ms per FP32 pass, 0.611 ms at 6
+// blocks (64 registers, spills); before the rows went through L2, 0.664 ms against 0.697 ms
+// unbounded (4 blocks).
 template <class R, bool kPf>
 __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
     int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, const R* __restrict__ QA,
@@ -227,12 +232,12 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
       mbar_init(bar);
       const uint32_t ab = 9u * K * kTile * sizeof(R),
                      bb = bulk_b<R>() ? 4u * S * kTile * sizeof(R) : 0u;
-      mbar_expect_tx(bar, ab + bb);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(Ag), "r"(ab) : "memory");
+      mbar_expect_tx(bar, bb);
       // withhold != 0 (the timeout test of gks_debug_recon_wait): no copy is issued, so the
       // barrier's phase never completes and the bounded wait below runs out with nothing in
       // flight
       if (!withhold) {
-        bulk_load(smem_raw + L.a_off, Ag, ab, bar);
         if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
       }
     }
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
       if (threadIdx.x == 0) atomicOr(flag, kErrTimeout);
       return;
     }
-    A = reinterpret_cast<const R*>(smem_raw + L.a_off) + lane;
+    A = Ag + lane;
     Bt = bulk_b<R>() ? reinterpret_cast<const R*>(smem_raw + L.b_off) + lane : Bg + lane;
   } else {
     __syncthreads();
@@ -295,19 +300,31 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
     Bt = Bg + lane;
   }
 
-  // phase 2: rows n = warp, warp + 5 of a = A+ dq, and the sub-stencil fits b_m with their
+  // phase 2: rows n = warp, warp + 5 of a = A+ dq (both in one member loop: each stencil
+  // difference is read once for the two rows), and the sub-stencil fits b_m with their
   // indicators beta_m = |b_m|^2 (scaled coordinates); sub-stencils go to the warps in reverse
   // order (m = 4 - warp, 9 - warp) so that the warp with one row takes two of them
-  for (int n = warp; n < 9; n += kReconWarps) {
-    R acc[5] = {R(0), R(0), R(0), R(0), R(0)};
-#pragma unroll 4
+  {
+    const int n0 = warp, n1 = warp + kReconWarps;
+    const bool two = n1 < 9;
+    const int n1c = two ? n1 : n0;
+    R acc0[5] = {R(0), R(0), R(0), R(0), R(0)}, acc1[5] = {R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll 6
     for (int k = 0; k < K; ++k) {
-      const R row = kPf ? A[(9 * k + n) * kTile] : __ldg(A + (9 * k + n) * kTile);
+      const R r0 = __ldg(A + (9 * k + n0) * kTile);
+      const R r1 = __ldg(A + (9 * k + n1c) * kTile);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] += row * sdq[(5 * k + v) * kTile + lane];
+      for (int v = 0; v < 5; ++v) {
+        const R d = sdq[(5 * k + v) * kTile + lane];
+        acc0[v] += r0 * d;
+        acc1[v] += r1 * d;
+      }
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sa[(5 * n + v) * kTile + lane] = acc[v];
+    for (int v = 0; v < 5; ++v) {
+      sa[(5 * n0 + v) * kTile + lane] = acc0[v];
+      if (two) sa[(5 * n1 + v) * kTile + lane] = acc1[v];
+    }
   }
   for (int s = kReconWarps - 1 - warp; s < Mt; s += kReconWarps) {
     int slot = 0;

@@ -1,11 +1,11 @@
 """Failure detection on the GPU without faulting it.
 
-The reconstruction stages its pseudo-inverse rows and sub-stencil entries into shared memory by
-bulk copies completed on an mbarrier, and every thread waits for them with a bounded number of
-tries; when the wait runs out, the block sets the timeout bit of the solver's status word and
-returns. The test hook gks_debug_recon_wait withholds the copies (nothing is in flight, so the
-barrier simply never completes) with a limit of a few dozen tries: the status check must
-report GKS_E_TIMEOUT, and the same solver must then compute a normal residual.
+The FP32 reconstruction stages its sub-stencil entries into shared memory by a bulk copy
+completed on an mbarrier, and every thread waits for it with a bounded number of tries; when
+the wait runs out, the block sets the timeout bit of the solver's status word and returns. The
+test hook gks_debug_recon_wait withholds the copy (nothing is in flight, so the barrier simply
+never completes) with a limit of a few dozen tries: the status check must report
+GKS_E_TIMEOUT, and the same solver must then compute a normal residual.
 """
 import numpy as np
 import pytest
@@ -34,7 +34,7 @@ def test_bounded_wait_times_out_and_the_solver_recovers():
     m = I.layered_box_mesh(3, "hex")  # 27 cells: one 32-cell tile
     om = oracle.Mesh(m)
     Q = I.perturbed_state(om.advection_average(), seed=61, amp=0.02)
-    S = gks.Solver(m)
+    S = gks.Solver(m, precision=gks.GKS_PREC_MIXED)
     L0, Lt0 = S.residual(Q, 0.01)
     gks.gks_debug_recon_wait(S.h, 32, True)
     with pytest.raises(gks.GksError) as e:
@@ -50,7 +50,7 @@ def test_bounded_wait_times_out_and_the_solver_recovers():
     L1, Lt1 = S.residual(Q, 0.01)
     assert torch.equal(L0, L1) and torch.equal(Lt0, Lt1)
     Lo, _ = om.residual(oracle.params_vec(), Q, 0.01)
-    assert rel(L1.cpu().numpy(), Lo) < 1e-12
+    assert rel(L1.cpu().numpy(), Lo) < 2e-4  # the mixed path's residual tolerance
     # a short limit that the copies meet in time changes nothing
     gks.gks_debug_recon_wait(S.h, 1 << 16, False)
     L2, _ = S.residual(Q, 0.01)

@@ -291,3 +291,29 @@ def test_cell_order_leaves_results_bitwise():
         S.close()
     for k in (1, 2):
         assert all(torch.equal(a, b) for a, b in zip(out[0], out[k]))
+
+
+@pytest.mark.parametrize("prec", [gks.GKS_PREC_FP64, gks.GKS_PREC_MIXED, gks.GKS_PREC_MIXED_FP64UPD])
+def test_checkpoint_and_resume_are_bitwise(prec):
+    """The state (Q, t, step) is the whole checkpoint: reading it out after k steps and setting
+    it into a fresh solver continues bit for bit like the uninterrupted run (the float-float
+    state of the mixed path round-trips through its FP64 form exactly)."""
+    m, om = mesh_pair()
+    Q = smooth_state(m, om, seed=18)
+    p = CASES["full_viscous"]
+    dt = 0.004
+    A = gks.Solver(m, precision=prec, **p)
+    A.set_state(Q)
+    A.step(dt, 5)
+    ref = A.get_state()
+    B = gks.Solver(m, precision=prec, **p)
+    B.set_state(Q)
+    B.step(dt, 2)
+    ckpt = B.get_state().cpu().numpy()
+    B.close()
+    C = gks.Solver(m, precision=prec, **p)
+    C.set_state(ckpt)
+    C.step(dt, 3)
+    assert torch.equal(C.get_state(), ref)
+    A.close()
+    C.close()
