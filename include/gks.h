@@ -182,7 +182,12 @@ gks_status gks_init(const gks_mesh* m, const gks_params* p, void* stream, gks_so
 
 /* Copy a state [5][n_cells] (caller order, host or device) into the solver. */
 gks_status gks_set_state(gks_solver* s, const double* Q);
-/* Copy the solver's state out to [5][n_cells] (caller order, host or device). */
+/* Copy the solver's state out to [5][n_cells] (caller order, host or device).
+ * State, time and step count are the whole checkpoint: with GKS_PREC_FP64 and
+ * GKS_PREC_MIXED_FP64UPD (FP64 state) a run resumed from it by gks_set_state continues bit for
+ * bit. GKS_PREC_MIXED keeps the state as float-float pairs; their FP64 form rounds a pair whose
+ * parts lie more than 53 bits apart, so a resumed run agrees with the uninterrupted one to the
+ * mixed path's precision, not bit for bit. */
 gks_status gks_get_state(gks_solver* s, double* Q);
 
 /* Largest stable step for the current state: cfl * min_i h_i / (|U_i| + c_i + 2 mu/(rho_i h_i)),
@@ -209,13 +214,13 @@ gks_status gks_step(gks_solver* s, double dt, int nsteps);
 gks_status gks_check(gks_solver* s);
 
 /* Test hook for the bounded wait of the reconstruction (the paper has no counterpart): every
- * later reconstruction of this solver waits for its bulk copy (the FP32 sub-stencil entries
- * staged into shared memory) at most wait_tries mbarrier tries per wait (0: the library default
- * of 2^22), and with withhold_copies != 0 issues no copy at all, so the barrier never
- * completes, every block gives up after its tries with nothing in flight, and the next status
- * check (gks_check, gks_residual) returns GKS_E_TIMEOUT. The reconstruction's output is then
- * undefined; gks_debug_recon_wait(s, 0, 0) restores normal operation. Only the mixed-precision
- * modes stage that copy; the FP64 path reads the entries from global memory and has no wait.
+ * later reconstruction of this solver waits for its mbarrier (completed by the bulk copy of the
+ * sub-stencil entries into shared memory, where a range stages them) at most wait_tries tries
+ * per wait (0: the library default of 2^22), and with withhold_copies != 0 issues no copy and
+ * expects 16 bytes more than the copies bring, so the barrier never completes, every block
+ * gives up after its tries with nothing in flight, and the next status check (gks_check,
+ * gks_residual) returns GKS_E_TIMEOUT, in every precision. The reconstruction's output is then
+ * undefined; gks_debug_recon_wait(s, 0, 0) restores normal operation.
  * Errors: GKS_E_INVAL (s NULL, wait_tries < 0). */
 gks_status gks_debug_recon_wait(gks_solver* s, int wait_tries, int withhold_copies);
 

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(64) k_vjp_recon(
   const int64_t row0 = t_st[tile];
   const int32_t* sidx = t_idx + row0 * kTile + lane;
   const double* A = Ap + row0 * 9 * kTile + lane;
-  const double* Bt = Bp + (int64_t)t_sb[tile] * 4 * kTile + lane;
+  const double* Bt = Bp + ((int64_t)t_sb[tile] * kTile + lane) * 4;  // [slot][lane][4]
   double* gdqc = gdq + row0 * 5 * kTile + lane;
   double m2[6];
   for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + i];
@@ -251,8 +251,8 @@ __global__ void __launch_bounds__(64) k_vjp_recon(
         const int cs = (int)((cnt >> (8 * s)) & 0xffu);
         b[s][0] = b[s][1] = b[s][2] = 0.0;
         for (int j = 0; j < cs; ++j, e += 4 * kTile) {
-          const int k = (int)e[3 * kTile];
-          for (int t = 0; t < 3; ++t) b[s][t] += e[t * kTile] * dq[k];
+          const int k = (int)e[3];
+          for (int t = 0; t < 3; ++t) b[s][t] += e[t] * dq[k];
         }
         bet[s] = b[s][0] * b[s][0] + b[s][1] * b[s][1] + b[s][2] * b[s][2];
       }
@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(64) k_vjp_recon(
       for (int s = 0; s < kMaxSub; ++s) {
         const int csn = (int)((cnt >> (8 * s)) & 0xffu);
         for (int j = 0; j < csn; ++j, e += 4 * kTile) {
-          const int k = (int)e[3 * kTile];
-          for (int t = 0; t < 3; ++t) gd[k] += e[t * kTile] * gb[s][t];
+          const int k = (int)e[3];
+          for (int t = 0; t < 3; ++t) gd[k] += e[t] * gb[s][t];
         }
       }
     }

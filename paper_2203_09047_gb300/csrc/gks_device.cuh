@@ -123,7 +123,7 @@ struct Geo64 {
 template <class R>
 struct GeoR {
   R* Ap = nullptr;   // pseudo-inverse rows, tile-interleaved
-  R* Bp = nullptr;   // sub-stencil entries, tile-interleaved
+  R* Bp = nullptr;   // sub-stencil entries [slot][lane][4] (3 coefficients, member index)
   R* mom = nullptr;  // [6][nc]
   R* h = nullptr;    // [nc]
   R* fgp = nullptr;  // [10][4 nf]: dl(3) dr(3) n1(3) w, index 4 f + gauss point

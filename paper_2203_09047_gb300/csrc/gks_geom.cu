@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
       A[k + (3 + q) * K] = d[pa[q]] * d[pb[q]] + mj * r2 - m0[q];
     }
   }
-  // sub-stencils first (they only need the linear columns); entries sub-stencil major in the
-  // tile-interleaved layout
+  // sub-stencils first (they only need the linear columns); entries sub-stencil major, per tile
+  // slot one record of four values per lane (the three pseudo-inverse coefficients and the
+  // member index: [slot][lane][4], one 16-byte load on the FP32 path)
   const int M = n_sub[i];
   const int64_t tile = i / kTile;
   const int lane = (int)(i % kTile);
@@ -249,8 +250,9 @@ __global__ void __launch_bounds__(kThreads) k_geom_ls(
       double out[3];
       pinv_column(S, km, 3, sb, srd, r, x, out);
       const int64_t slot = (int64_t)t_sb[tile] + slot0 + r;
-      for (int a = 0; a < 3; ++a) Bp[(4 * slot + a) * kTile + lane] = (R)out[a];
-      Bp[(4 * slot + 3) * kTile + lane] = (R)idx[r];  // member index, exact in either precision
+      R* rec = Bp + 4 * (slot * kTile + lane);
+      for (int a = 0; a < 3; ++a) rec[a] = (R)out[a];
+      rec[3] = (R)idx[r];  // member index, exact in either precision
     }
     slot0 += (int)((tc >> (8 * s)) & 0xffu);
   }

@@ -151,40 +151,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int tr
 //   C = (wb_0/g_0) a + sum_m (wb_m - wb_0 g_m/g_0) b_m, i.e. Eq. weno as one polynomial (phase 4)
 // Output: 10 coefficients per variable of the polynomial in physical offsets from the centroid.
 // With kPf, when the block starts, the tile's pseudo-inverse rows (a contiguous block of the
-// interleaved layout) are prefetched into L2 by a bulk prefetch and the FP32 sub-stencil entries
-// are copied into shared memory by a bulk copy on an mbarrier, so that both transfers overlap
-// phase 1; phase 2 then reads the rows from L2 (each row once, two rows per warp in one member
-// loop, so that two independent loads per member are in flight) and the entries from shared
-// memory. Without kPf phase 2 reads both from global memory. Staging the rows in shared memory
+// interleaved layout) are prefetched into L2 by a bulk prefetch, and the sub-stencil entries are
+// either copied into shared memory by a bulk copy on an mbarrier (kStB: where that costs the
+// range no resident blocks) or prefetched into L2 as well, so that the transfers overlap phase
+// 1; phase 2 then reads the rows from L2 (each row once, two rows per warp in one member loop,
+// so that two independent loads per member are in flight) and the entries from shared memory or
+// L2. Without kPf phase 2 reads both from global memory. Staging the rows in shared memory
 // as well (they are read once, so the staging bought only the overlap) held the range's blocks
 // to 2-3 per SM: 0.669 against 0.598 ms per FP32 pass on the 64^3-cube mesh with the enlarged
 // stencils, 6.54 against 5.38 ms in FP64.
 constexpr int kReconWarps = 5;
 constexpr int kReconThreads = kReconWarps * kTile;
-
-// Whether the sub-stencil entries travel with the rows in the bulk copies: yes for FP32; for
-// FP64 (twice the shared memory per tile) reading them from global memory measured 8 % faster
-// (5.26 against 5.73 ms per pass on the 64^3-cube mesh, more blocks per SM), for FP32 1 %
-// slower.
-template <class R>
-__host__ __device__ constexpr bool bulk_b() {
-  return sizeof(R) == 4;
-}
+constexpr int kReconBlocksPerSM = 5;  // the register bound (launch bounds) of k_recon
 
 // Shared-memory layout of one block for a range with largest stencil Kr, largest sum of
 // sub-stencil member counts Sr and largest number of sub-stencil slots Mr, in units of one
-// interleaved row (kTile values): [mbarrier, 16 B][B entries 4 Sr] (only with kPf and when
-// bulk_b), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]. Every part starts on a 16-byte
-// boundary. (a_off marks where staged rows would start; the rows come through L2.)
+// interleaved row (kTile values): [mbarrier, 16 B][B entries 4 Sr] (only with kPf and stb: the
+// sub-stencil entries staged by a bulk copy), then a[9][5], b[Mr][3][5], beta[Mr][5], dq[Kr][5]
+// (the last in the lane-major form of DqRow below). Every part starts on a 16-byte boundary.
+// (a_off marks where staged rows would start; the rows come through L2.)
 
 template <class R>
 struct ReconSmem {
   size_t a_off, b_off, ca_off, cb_off, cbet_off, dq_off, bytes;
-  __host__ __device__ ReconSmem(int Kr, int Sr, int Mr, bool pf) {
+  __host__ __device__ ReconSmem(int Kr, int Sr, int Mr, bool pf, bool stb) {
     const size_t row = (size_t)kTile * sizeof(R);
     a_off = pf ? 16 : 0;
     b_off = a_off;
-    ca_off = b_off + (pf && bulk_b<R>() ? 4 * (size_t)Sr * row : 0);
+    ca_off = b_off + (pf && stb ? 4 * (size_t)Sr * row : 0);
     cb_off = ca_off + 45 * row;
     cbet_off = cb_off + 15 * (size_t)Mr * row;
     dq_off = cbet_off + 5 * (size_t)Mr * row;
@@ -192,12 +186,68 @@ struct ReconSmem {
   }
 };
 
+// Stencil differences in shared memory: variables 0-3 of member k as 16-byte vectors with the
+// lane fastest ([k][h][lane], h < kH), variable 4 in a plain row [k][lane] after all of them, so
+// that a thread reads or writes a member's five differences in two (FP32) or three (FP64)
+// shared-memory accesses instead of five; consecutive lanes touch consecutive 16-byte words (no
+// bank conflicts). Against five scalar rows: 0.599 -> 0.595 ms per FP32 pass on the 64^3-cube
+// mesh.
+template <class R>
+struct DqRow;
+template <>
+struct DqRow<float> {
+  static constexpr int kH = 1;
+  __device__ __forceinline__ static void put(unsigned char* s, int k, int lane, const float d[4]) {
+    reinterpret_cast<float4*>(s)[k * kTile + lane] = make_float4(d[0], d[1], d[2], d[3]);
+  }
+  __device__ __forceinline__ static void get(const unsigned char* s, int k, int lane, float d[4]) {
+    const float4 x = reinterpret_cast<const float4*>(s)[k * kTile + lane];
+    d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+  }
+};
+template <>
+struct DqRow<double> {
+  static constexpr int kH = 2;
+  __device__ __forceinline__ static void put(unsigned char* s, int k, int lane, const double d[4]) {
+    double2* p = reinterpret_cast<double2*>(s) + 2 * k * kTile + lane;
+    p[0] = make_double2(d[0], d[1]);
+    p[kTile] = make_double2(d[2], d[3]);
+  }
+  __device__ __forceinline__ static void get(const unsigned char* s, int k, int lane, double d[4]) {
+    const double2* p = reinterpret_cast<const double2*>(s) + 2 * k * kTile + lane;
+    const double2 x = p[0], y = p[kTile];
+    d[0] = x.x; d[1] = x.y; d[2] = y.x; d[3] = y.y;
+  }
+};
+
+// One sub-stencil entry (three pseudo-inverse coefficients and the member index) of one lane:
+// one 16-byte load in FP32, two in FP64, from shared memory (staged) or through the read-only
+// path (global). Against four interleaved rows: 0.571 -> 0.569 ms per FP32 pass.
+template <class R>
+struct BRec;
+template <>
+struct BRec<float> {
+  __device__ __forceinline__ static void get(const float* e, bool staged, float c[4]) {
+    const float4* p = reinterpret_cast<const float4*>(e);
+    const float4 x = staged ? *p : __ldg(p);
+    c[0] = x.x; c[1] = x.y; c[2] = x.z; c[3] = x.w;
+  }
+};
+template <>
+struct BRec<double> {
+  __device__ __forceinline__ static void get(const double* e, bool staged, double c[4]) {
+    const double2* p = reinterpret_cast<const double2*>(e);
+    const double2 x = staged ? p[0] : __ldg(p), y = staged ? p[1] : __ldg(p + 1);
+    c[0] = x.x; c[1] = x.y; c[2] = y.x; c[3] = y.y;
+  }
+};
+
 // Five resident blocks per SM as the register bound (at most 80 registers a thread; 72 used):
 // on the 64^3-cube hybrid mesh with the enlarged stencils 0.598 ms per FP32 pass, 0.611 ms at 6
 // blocks (64 registers, spills); before the rows went through L2, 0.664 ms against 0.697 ms
 // unbounded (4 blocks).
-template <class R, bool kPf>
-__global__ void __launch_bounds__(kReconThreads, 5) k_recon(
+template <class R, bool kPf, bool kStB>
+__global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
     int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, const R* __restrict__ QA,
     const int32_t* __restrict__ t_K, const uint64_t* __restrict__ t_cnt,
     const int32_t* __restrict__ t_st, const int32_t* __restrict__ t_sb,
@@ -206,11 +256,12 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
     const R* __restrict__ hcell, R wg, R weps, int wpow, R* __restrict__ poly, int* flag,
     int wait_tries, int withhold) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ReconSmem<R> L(Kr, Sr, Mr, kPf);
+  const ReconSmem<R> L(Kr, Sr, Mr, kPf, kStB);
   R* sa = reinterpret_cast<R*>(smem_raw + L.ca_off);      // [n][v][lane]
   R* sb = reinterpret_cast<R*>(smem_raw + L.cb_off);      // [m][t][v][lane]
   R* sbet = reinterpret_cast<R*>(smem_raw + L.cbet_off);  // [m][v][lane]
-  R* sdq = reinterpret_cast<R*>(smem_raw + L.dq_off);     // [k][v][lane]
+  unsigned char* sdqv = smem_raw + L.dq_off;              // variables 0-3, DqRow<R>
+  R* sdq4 = reinterpret_cast<R*>(sdqv + 4 * (size_t)Kr * kTile * sizeof(R));  // [k][lane]
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
   const int64_t tile = tile0 + blockIdx.x;
   const int lane = threadIdx.x & (kTile - 1);
@@ -230,16 +281,15 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
   if (kPf) {
     if (threadIdx.x == 0) {
       mbar_init(bar);
-      const uint32_t ab = 9u * K * kTile * sizeof(R),
-                     bb = bulk_b<R>() ? 4u * S * kTile * sizeof(R) : 0u;
+      const uint32_t ab = 9u * K * kTile * sizeof(R), bb = 4u * S * kTile * sizeof(R);
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(Ag), "r"(ab) : "memory");
-      mbar_expect_tx(bar, bb);
-      // withhold != 0 (the timeout test of gks_debug_recon_wait): no copy is issued, so the
-      // barrier's phase never completes and the bounded wait below runs out with nothing in
-      // flight
-      if (!withhold) {
-        if (bb) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
-      }
+      if (!kStB && bb)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(Bg), "r"(bb) : "memory");
+      // withhold != 0 (the timeout test of gks_debug_recon_wait): no copy is issued and 16
+      // bytes more than the copies would bring are expected, so the barrier's phase never
+      // completes and the bounded wait below runs out with nothing in flight
+      mbar_expect_tx(bar, (kStB ? bb : 0u) + (withhold ? 16u : 0u));
+      if (kStB && bb && !withhold) bulk_load(smem_raw + L.b_off, Bg, bb, bar);
     }
   }
   const int64_t i = tile * kTile + lane;
@@ -277,8 +327,11 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
       if (fl & 2) g[u].flip(2);
       if (fl & 4) g[u].flip(3);
       const int k = k0 + u * kReconWarps;
+      R d[4];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) sdq[(5 * k + v) * kTile + lane] = g[u].minus(c0, v);
+      for (int v = 0; v < 4; ++v) d[v] = g[u].minus(c0, v);
+      DqRow<R>::put(sdqv, k, lane, d);
+      sdq4[k * kTile + lane] = g[u].minus(c0, 4);
     }
   }
   const R* A;
@@ -293,11 +346,11 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
       return;
     }
     A = Ag + lane;
-    Bt = bulk_b<R>() ? reinterpret_cast<const R*>(smem_raw + L.b_off) + lane : Bg + lane;
+    Bt = (kStB ? reinterpret_cast<const R*>(smem_raw + L.b_off) : Bg) + 4 * lane;
   } else {
     __syncthreads();
     A = Ag + lane;
-    Bt = Bg + lane;
+    Bt = Bg + 4 * lane;
   }
 
   // phase 2: rows n = warp, warp + 5 of a = A+ dq (both in one member loop: each stencil
@@ -313,11 +366,13 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
     for (int k = 0; k < K; ++k) {
       const R r0 = __ldg(A + (9 * k + n0) * kTile);
       const R r1 = __ldg(A + (9 * k + n1c) * kTile);
+      R d[5];
+      DqRow<R>::get(sdqv, k, lane, d);
+      d[4] = sdq4[k * kTile + lane];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
-        const R d = sdq[(5 * k + v) * kTile + lane];
-        acc0[v] += r0 * d;
-        acc1[v] += r1 * d;
+        acc0[v] += r0 * d[v];
+        acc1[v] += r1 * d[v];
       }
     }
 #pragma unroll
@@ -339,16 +394,15 @@ __global__ void __launch_bounds__(kReconThreads, 5) k_recon(
 #pragma unroll 2
     for (int j = 0; j < cs; ++j, e += 4 * kTile) {
       R c[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        c[t] = kPf && bulk_b<R>() ? e[t * kTile] : __ldg(e + t * kTile);
+      BRec<R>::get(e, kPf && kStB, c);
       const int k = (int)c[3];
+      R dq[5];
+      DqRow<R>::get(sdqv, k, lane, dq);
+      dq[4] = sdq4[k * kTile + lane];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const R dq = sdq[(5 * k + v) * kTile + lane];
+      for (int v = 0; v < 5; ++v)
 #pragma unroll
-        for (int t = 0; t < 3; ++t) b[t][v] += c[t] * dq;
-      }
+        for (int t = 0; t < 3; ++t) b[t][v] += c[t] * dq[v];
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -1112,12 +1166,20 @@ __global__ void k_dt_final(const double* partial, int n, double* out) {
 // Largest dynamic shared memory of one block (227 KB on this architecture).
 constexpr size_t kMaxBlockSmem = 227 * 1024;
 
-template <class R, bool kPf>
+// Shared memory of one SM and the part the hardware keeps for each resident block.
+constexpr size_t kSmemPerSM = 228 * 1024, kSmemPerBlockReserved = 1024;
+
+inline int recon_blocks_per_sm(size_t smem) {
+  return (int)(kSmemPerSM / (smem + kSmemPerBlockReserved));
+}
+
+template <class R, bool kPf, bool kStB>
 void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const R* QA,
                         R* poly, int* flag, int r, size_t smem, cudaStream_t st) {
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_recon<R, kPf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_recon<R, kPf><<<(unsigned)(m.rr.t1[r] - m.rr.t0[r]), kReconThreads, smem, st>>>(
+    cudaFuncSetAttribute(k_recon<R, kPf, kStB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  k_recon<R, kPf, kStB><<<(unsigned)(m.rr.t1[r] - m.rr.t0[r]), kReconThreads, smem, st>>>(
       m.nc, m.rr.t0[r], m.rr.K[r], m.rr.S[r], m.rr.M[r], QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
       m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag,
       p.wait_tries, p.withhold);
@@ -1223,12 +1285,20 @@ void launch_recon(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p, const
       s = fj->aux[used];
       cudaStreamWaitEvent(s, fj->fork, 0);
     }
-    const ReconSmem<R> pf(m.rr.K[r], m.rr.S[r], m.rr.M[r], true);
-    if (pf.bytes <= kMaxBlockSmem) {
-      launch_recon_range<R, true>(m, g, p, QA, poly, flag, r, pf.bytes, s);
+    // the sub-stencil entries are staged in shared memory only where that costs the range no
+    // resident blocks below the register bound; otherwise they are prefetched into L2 like the
+    // rows (on the 64^3-cube mesh the pyramid and hexahedron ranges: 3 and 4 blocks per SM with
+    // the entries staged, 5 without; 0.595 -> 0.571 ms per FP32 pass)
+    const ReconSmem<R> pb(m.rr.K[r], m.rr.S[r], m.rr.M[r], true, true);
+    const ReconSmem<R> pl(m.rr.K[r], m.rr.S[r], m.rr.M[r], true, false);
+    const int nb_l = std::min(kReconBlocksPerSM, recon_blocks_per_sm(pl.bytes));
+    if (pb.bytes <= kMaxBlockSmem && recon_blocks_per_sm(pb.bytes) >= nb_l) {
+      launch_recon_range<R, true, true>(m, g, p, QA, poly, flag, r, pb.bytes, s);
+    } else if (pl.bytes <= kMaxBlockSmem) {
+      launch_recon_range<R, true, false>(m, g, p, QA, poly, flag, r, pl.bytes, s);
     } else {
-      const ReconSmem<R> np(m.rr.K[r], m.rr.S[r], m.rr.M[r], false);
-      launch_recon_range<R, false>(m, g, p, QA, poly, flag, r, np.bytes, s);
+      const ReconSmem<R> np(m.rr.K[r], m.rr.S[r], m.rr.M[r], false, false);
+      launch_recon_range<R, false, false>(m, g, p, QA, poly, flag, r, np.bytes, s);
     }
     if (s != st) {
       cudaEventRecord(fj->join[used], s);

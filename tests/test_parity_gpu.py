@@ -294,10 +294,13 @@ def test_cell_order_leaves_results_bitwise():
 
 
 @pytest.mark.parametrize("prec", [gks.GKS_PREC_FP64, gks.GKS_PREC_MIXED, gks.GKS_PREC_MIXED_FP64UPD])
-def test_checkpoint_and_resume_are_bitwise(prec):
+def test_checkpoint_and_resume(prec):
     """The state (Q, t, step) is the whole checkpoint: reading it out after k steps and setting
-    it into a fresh solver continues bit for bit like the uninterrupted run (the float-float
-    state of the mixed path round-trips through its FP64 form exactly)."""
+    it into a fresh solver continues bit for bit like the uninterrupted run when the state is
+    FP64. The mixed path's float-float state has up to 48 significant bits spread over more than
+    53 when the low part is small, so its FP64 form can round it: the resumed run then agrees to
+    the mixed path's own step tolerance, and a checkpoint that round-trips exactly (set, get)
+    resumes identically from there on."""
     m, om = mesh_pair()
     Q = smooth_state(m, om, seed=18)
     p = CASES["full_viscous"]
@@ -314,6 +317,18 @@ def test_checkpoint_and_resume_are_bitwise(prec):
     C = gks.Solver(m, precision=prec, **p)
     C.set_state(ckpt)
     C.step(dt, 3)
-    assert torch.equal(C.get_state(), ref)
+    if prec == gks.GKS_PREC_MIXED:
+        assert rel(C.get_state().cpu(), ref.cpu()) < MIXED_TOL_STEP
+        # from a state that is its own FP64 form, two solvers resume identically
+        q1 = C.get_state().cpu().numpy()
+        D, E = (gks.Solver(m, precision=prec, **p) for _ in range(2))
+        for X in (D, E):
+            X.set_state(q1)
+            X.step(dt, 2)
+        assert torch.equal(D.get_state(), E.get_state())
+        D.close()
+        E.close()
+    else:
+        assert torch.equal(C.get_state(), ref)
     A.close()
     C.close()
