@@ -492,16 +492,16 @@ def run_gpu(args):
     # 48^3-cube mesh with the enlarged stencils (profiles/k_recon_float_advection48_ncu.md),
     # scaled by cells (same layer pattern and stencils); the flux kernel has changed since its
     # capture, so it reports no traffic
-    dram_per_unit = {"recon": (1569.7, nc)}
+    dram_per_unit = {"recon": (1554.2, nc)}
 
-    def roof_for(table, is_mixed):
-        dom = max(table, key=lambda k: table[k]["share"] or 0)
+    def roof_of(table, dom, is_mixed):
         if dom == "flux":
             peak = fp32_peak if is_mixed else fp64_peak
             ach = table["flux"]["tflops"]
             return {"kernel": f"k_flux<{'float' if is_mixed else 'double'}>", "bound": "alu",
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": (dram_per_unit["flux"][0] * dram_per_unit["flux"][1]) if is_mixed else None,
+                    "traffic": (dram_per_unit["flux"][0] * dram_per_unit["flux"][1])
+                               if is_mixed and "flux" in dram_per_unit else None,
                     "peak_source": f"measured {'FP32' if is_mixed else 'FP64'} FMA throughput of "
                                    "this GPU (gks_alu_peaks, an FMA as 2 flops)",
                     "flops_per_gauss_point": flops_gp, "special_per_gauss_point": special_gp}
@@ -514,6 +514,13 @@ def run_gpu(args):
                 "per": "one pass over the mesh (one launch per cell-kind tile range)" if dom == "recon"
                        else "one launch"}
 
+    def roof_for(table, is_mixed):
+        """The dominant kernel's roofline (largest share of the step's kernel time)."""
+        return roof_of(table, max(table, key=lambda k: table[k]["share"] or 0), is_mixed)
+
+    def rooflines(table, is_mixed):
+        return {k: roof_of(table, k, is_mixed) for k in ("recon", "flux")}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
@@ -522,6 +529,7 @@ def run_gpu(args):
         "clocks": mixed["clocks"],
         "gpu_launches": int(sum(c * l for c, l in zip(mixed["kcnt"], gks.gks_launches_per_pass(S.h)))),
         "roofline": roof_for(kt, True),
+        "rooflines": rooflines(kt, True),
         "kernels": kt,
         "fp64": {"value": v64, "unit": UNIT, "steps": fp64_steps, "ms_per_step": fp64["ms"] / fp64_steps,
                  "dtype": "f64", "roofline": roof_for(kt64, False), "kernels": kt64,
