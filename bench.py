@@ -488,11 +488,11 @@ def run_gpu(args):
     for k, name in enumerate(["recon", "flux", "gather"]):
         kt64[name]["gbs"] = bytes64[k] / (kt64[name]["avg_ms"] * 1e-3) / 1e9
 
-    # DRAM bytes (read + write) per pass of the FP32 reconstruction from the ncu capture on the
-    # 48^3-cube mesh with the enlarged stencils (profiles/k_recon_float_advection48_ncu.md),
-    # scaled by cells (same layer pattern and stencils); the flux kernel has changed since its
-    # capture, so it reports no traffic
-    dram_per_unit = {"recon": (1554.2, nc)}
+    # DRAM bytes (read + write) per pass of the FP32 reconstruction and per launch of the FP32
+    # smooth flux from the ncu captures on the 48^3-cube mesh with the enlarged stencils
+    # (profiles/k_recon_float_advection48_ncu.md, profiles/k_flux_float_smooth_advection48_ncu.md),
+    # scaled by cells and by faces (same layer pattern and stencils)
+    dram_per_unit = {"recon": (1554.2, nc), "flux": (296.9, nf)}
 
     def roof_of(table, dom, is_mixed):
         if dom == "flux":

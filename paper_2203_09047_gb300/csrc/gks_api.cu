@@ -650,6 +650,23 @@ gks_status gks_init(const gks_mesh* mesh, const gks_params* p, void* stream, gks
     r.S[r.n - 1] = std::max(r.S[r.n - 1], S);
     r.M[r.n - 1] = std::max(r.M[r.n - 1], M);
   }
+  // a range is uniform when all its tiles match the first one's stencil size and sub-stencil
+  // counts (then t_st and t_sb grow by K and S per tile, and the kernel needs no table loads)
+  for (int k = 0; k < m.rr.n; ++k) {
+    TileRanges& r = m.rr;
+    const int64_t a = r.t0[k];
+    int S0 = 0;
+    for (int q = 0; q < kMaxSub; ++q) S0 += (int)((h.t_cnt[a] >> (8 * q)) & 0xffu);
+    bool uni = r.t1[k] > a;
+    for (int64_t t = a; t < r.t1[k] && uni; ++t)
+      uni = h.t_K[t] == h.t_K[a] && h.t_cnt[t] == h.t_cnt[a] &&
+            (int64_t)h.t_st[t] == (int64_t)h.t_st[a] + (t - a) * h.t_K[a] &&
+            (int64_t)h.t_sb[t] == (int64_t)h.t_sb[a] + (t - a) * S0;
+    r.uni[k] = uni ? 1 : 0;
+    r.cnt[k] = h.t_cnt[a];
+    r.st0[k] = h.t_st[a];
+    r.sb0[k] = h.t_sb[a];
+  }
   // auxiliary streams for the concurrent reconstruction ranges (serial if unavailable)
   if (m.rr.n > 1 && cudaEventCreateWithFlags(&s->fj.fork, cudaEventDisableTiming) == cudaSuccess) {
     for (int k = 0; k < m.rr.n - 1; ++k) {

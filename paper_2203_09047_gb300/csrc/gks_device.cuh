@@ -50,6 +50,11 @@ struct TileRanges {
   int n = 0;
   int64_t t0[kMaxTileRanges] = {}, t1[kMaxTileRanges] = {};
   int K[kMaxTileRanges] = {}, S[kMaxTileRanges] = {}, M[kMaxTileRanges] = {};
+  // uniform ranges: every tile has the first tile's stencil size and sub-stencil counts, so
+  // the tile's offsets into the interleaved arrays follow from its index
+  int uni[kMaxTileRanges] = {};
+  uint64_t cnt[kMaxTileRanges] = {};
+  int64_t st0[kMaxTileRanges] = {}, sb0[kMaxTileRanges] = {};
 };
 
 // Mesh arrays on the device (internal order).

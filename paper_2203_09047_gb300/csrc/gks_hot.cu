@@ -283,9 +283,18 @@ struct PolyPair<double> {
 // on the 64^3-cube hybrid mesh with the enlarged stencils 0.598 ms per FP32 pass, 0.611 ms at 6
 // blocks (64 registers, spills); before the rows went through L2, 0.664 ms against 0.697 ms
 // unbounded (4 blocks).
+// A uniform range (every tile with the same stencil size K and sub-stencil counts cnt): the
+// tile's offsets into the interleaved arrays are st0 + K (tile - tile0) and sb0 + S (tile - tile0),
+// so no table load stands between the block's start and its first stencil gathers.
+struct ReconUni {
+  int on, K, S;
+  uint64_t cnt;
+  int64_t st0, sb0;
+};
+
 template <class R, bool kPf, bool kStB>
 __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
-    int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, const R* __restrict__ QA,
+    int64_t nc, int64_t tile0, int Kr, int Sr, int Mr, ReconUni u, const R* __restrict__ QA,
     const int32_t* __restrict__ t_K, const uint64_t* __restrict__ t_cnt,
     const int32_t* __restrict__ t_st, const int32_t* __restrict__ t_sb,
     const int32_t* __restrict__ t_idx, const int8_t* __restrict__ n_sub,
@@ -303,9 +312,11 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
   const int64_t tile = tile0 + blockIdx.x;
   const int lane = threadIdx.x & (kTile - 1);
   const int warp = threadIdx.x / kTile;
-  const int K = __ldg(t_K + tile);
-  const uint64_t cnt = __ldg(t_cnt + tile);
-  const int64_t st = __ldg(t_st + tile), sbo = __ldg(t_sb + tile);
+  const int64_t tl = tile - tile0;
+  const int K = u.on ? u.K : __ldg(t_K + tile);
+  const uint64_t cnt = u.on ? u.cnt : __ldg(t_cnt + tile);
+  const int64_t st = u.on ? u.st0 + tl * u.K : (int64_t)__ldg(t_st + tile);
+  const int64_t sbo = u.on ? u.sb0 + tl * u.S : (int64_t)__ldg(t_sb + tile);
   const R* Ag = Ap + st * 9 * kTile;
   const R* Bg = Bp + sbo * 4 * kTile;
   int S = 0, Mt = 0;  // entries and sub-stencil slots of this tile
@@ -332,12 +343,17 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
   const int64_t i = tile * kTile + lane;
   const bool valid = i < nc;
   const int64_t ic = valid ? i : tile * kTile;  // padded lanes mirror the tile's first cell
-  // per-cell data of the later phases, loaded now so that it arrives during phase 1
+  // per-cell data of the later phases: the moments and the cell size are prefetched into L2 now
+  // and loaded in phase 3 (held in registers through phases 1 and 2 they cost spills: 0.437
+  // against 0.470 ms per FP32 pass on the 64^3-cube mesh with the uniform-range offsets, 0.456
+  // against 0.457 without them)
   const int M = n_sub[ic];
-  R m2[6];
+  if (warp == 0) {
 #pragma unroll
-  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + ic];
-  const R hc = hcell[ic];
+    for (int q = 0; q < 6; ++q)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(mom + q * nc + ic));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(hcell + ic));
+  }
   const int32_t* sidx = t_idx + st * kTile + lane;
   Gq<R> c0;
   c0.load(QA, ic);
@@ -451,6 +467,10 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
   __syncthreads();
 
   // phase 3: nonlinear weights, variable v = warp
+  R m2[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) m2[q] = mom[q * nc + ic];
+  const R hc = hcell[ic];
   const R g0 = R(1) - wg * R(M);
   const int v = warp;
   {
@@ -547,13 +567,24 @@ struct PolyRef {
 };
 // A variable's ten coefficients as five pair loads (a cell's record starts on a 16-byte
 // boundary: kPolyStride values of 4 or 8 bytes; variable v at 10 v values).
+// In FP32 a variable's ten coefficients start on a 16-byte boundary for even v and on an 8-byte
+// one for odd v: three loads (16 + 16 + 8 or 8 + 16 + 16 bytes) instead of five.
 __device__ __forceinline__ void load_coefs(const PolyRef<float>& c, int v, float k[10]) {
-  const float2* q = reinterpret_cast<const float2*>(c.p + 10 * v);
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const float2 t = __ldg(q + i);
-    k[2 * i] = t.x;
-    k[2 * i + 1] = t.y;
+  const float* p = c.p + 10 * v;
+  if ((v & 1) == 0) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p + 4));
+    const float2 d = __ldg(reinterpret_cast<const float2*>(p + 8));
+    k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w;
+    k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+    k[8] = d.x; k[9] = d.y;
+  } else {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p + 2));
+    const float4 d = __ldg(reinterpret_cast<const float4*>(p + 6));
+    k[0] = a.x; k[1] = a.y;
+    k[2] = b.x; k[3] = b.y; k[4] = b.z; k[5] = b.w;
+    k[6] = d.x; k[7] = d.y; k[8] = d.z; k[9] = d.w;
   }
 }
 __device__ __forceinline__ void load_coefs(const PolyRef<double>& c, int v, double k[10]) {
@@ -598,6 +629,33 @@ __device__ __forceinline__ void first_order_if_nonphysical(const R* __restrict__
 #ifndef GKS_FLUX_FP64_MIN_BLOCKS
 #define GKS_FLUX_FP64_MIN_BLOCKS 1  // resident 128-thread blocks per SM, FP64 flux
 #endif
+// One 16-byte (FP32) or 32-byte (FP64) part of a face record of kFaceStride values: part j holds
+// values 4j .. 4j + 3 of acc (values 10 and 11 are padding, written as zeros).
+template <class R>
+struct FaceRec;
+template <>
+struct FaceRec<float> {
+  __device__ __forceinline__ static void put(float* rec, int j, const float acc[10]) {
+    float4 x;
+    if (j == 0) x = make_float4(acc[0], acc[1], acc[2], acc[3]);
+    else if (j == 1) x = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    else x = make_float4(acc[8], acc[9], 0.f, 0.f);
+    reinterpret_cast<float4*>(rec)[j] = x;
+  }
+};
+template <>
+struct FaceRec<double> {
+  __device__ __forceinline__ static void put(double* rec, int j, const double acc[10]) {
+    double2 x, y;
+    if (j == 0) { x = make_double2(acc[0], acc[1]); y = make_double2(acc[2], acc[3]); }
+    else if (j == 1) { x = make_double2(acc[4], acc[5]); y = make_double2(acc[6], acc[7]); }
+    else { x = make_double2(acc[8], acc[9]); y = make_double2(0.0, 0.0); }
+    double2* p = reinterpret_cast<double2*>(rec) + 2 * j;
+    p[0] = x;
+    p[1] = y;
+  }
+};
+
 template <class R, bool kFull, bool kTau0>
 __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS)
                                                       : GKS_FLUX_FP64_MIN_BLOCKS)
@@ -644,11 +702,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
     acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 2);
   }
-  if (active && (gid & 3) == 0) {
+  // every lane of the face now holds the sums; lanes 4f + j, j < 3, write the record's 16-byte
+  // part j (values 4j .. 4j + 3; the two padding values of part 2 are written as zeros), so a
+  // warp writes its eight faces' 384 contiguous bytes in one store
+  if (active && (gid & 3) < 3) {
     if (wall >= 0) wall_flux_fix(wall, wall_data(wall_tab, wall), acc);
-    R* o = fface + (int64_t)kFaceStride * f;
-#pragma unroll
-    for (int q = 0; q < 10; ++q) o[q] = acc[q];
+    FaceRec<R>::put(fface + (int64_t)kFaceStride * f, (int)(gid & 3), acc);
   }
 }
 
@@ -1229,8 +1288,9 @@ void launch_recon_range(const DevMesh& m, const GeoR<R>& g, const KParams<R>& p,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_recon<R, kPf, kStB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
+  ReconUni u{m.rr.uni[r], m.rr.K[r], m.rr.S[r], m.rr.cnt[r], m.rr.st0[r], m.rr.sb0[r]};
   k_recon<R, kPf, kStB><<<(unsigned)(m.rr.t1[r] - m.rr.t0[r]), kReconThreads, smem, st>>>(
-      m.nc, m.rr.t0[r], m.rr.K[r], m.rr.S[r], m.rr.M[r], QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
+      m.nc, m.rr.t0[r], m.rr.K[r], m.rr.S[r], m.rr.M[r], u, QA, m.t_K, m.t_cnt, m.t_st, m.t_sb,
       m.t_idx, m.n_sub, g.Ap, g.Bp, g.mom, g.h, p.weno_gamma, p.weno_eps, p.weno_pow, poly, flag,
       p.wait_tries, p.withhold);
 }
