@@ -10,6 +10,7 @@
 #include "gks_device.cuh"
 #include "gks_ff.cuh"
 #include "gks_kinetic.cuh"
+#include "gks_flux_f32x2.cuh"
 
 namespace gks {
 namespace {
@@ -622,9 +623,12 @@ __device__ __forceinline__ void first_order_if_nonphysical(const R* __restrict__
 // the axis least aligned with n1, n3 = n1 x n2), computes F^n and dF/dt, rotates back and
 // weights by the quadrature weight; the four are summed with shuffles and written once.
 // kFull selects the flux form and kTau0 a zero collision time at compile time, so that each
-// instance carries only the arithmetic (and registers) of its own form.
+// instance carries only the arithmetic (and registers) of its own form. The FP32 smooth
+// instances do the two sides' work on packed f32x2 arithmetic (gp_flux_global_smooth2); they
+// hold more values per thread, and 6 resident blocks measured best (0.453 ms per launch on the
+// 64^3-cube mesh; 5 and 7 blocks 0.454 and 0.460, the scalar form at 7 blocks 0.477).
 #ifndef GKS_FLUX_SMOOTH_MIN_BLOCKS
-#define GKS_FLUX_SMOOTH_MIN_BLOCKS 7  // resident 128-thread blocks per SM, FP32 smooth flux
+#define GKS_FLUX_SMOOTH_MIN_BLOCKS 6  // resident 128-thread blocks per SM, FP32 smooth flux
 #endif
 #ifndef GKS_FLUX_FP64_MIN_BLOCKS
 #define GKS_FLUX_FP64_MIN_BLOCKS 1  // resident 128-thread blocks per SM, FP64 flux
@@ -694,7 +698,12 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
     } else {
       wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);  // the wall's ghost
     }
-    if (!gp_flux_global(P, vl, gl, vr, gr, n1, w, dt, acc)) atomicOr(flag, kErrNonphysical);
+    bool ok;
+    if constexpr (sizeof(R) == 4 && !kFull)
+      ok = gp_flux_global_smooth2(P, vl, gl, vr, gr, n1, w, dt, acc);  // packed f32x2 sides
+    else
+      ok = gp_flux_global(P, vl, gl, vr, gr, n1, w, dt, acc);
+    if (!ok) atomicOr(flag, kErrNonphysical);
   }
   // sum the four Gauss points of the face (lanes 4f .. 4f+3 of one warp)
 #pragma unroll

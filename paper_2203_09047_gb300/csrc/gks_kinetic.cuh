@@ -495,6 +495,72 @@ GKS_HD void flux1_integrals(R tau, R d, R c[6]) {
   c[5] = -tau * tau * om;
 }
 
+// Interface-equilibrium terms of both flux forms from the interface state Q0 (primitives w0)
+// and its conserved-variable slopes dW_d along the local axes: the equilibrium time slope
+// rho0 <Ab psi>_0 = -sum_d rho0 <c_d ab_d psi>_0 = -sum_d A_d dW_d, the flux moments
+// E0 = rho0 <u psi>_0, E1 = rho0 <u (ab . c) psi>_0 = sum_d D T_d(W0)[dW_d] (only with a
+// collision-time model; zero otherwise, where tau = 0 multiplies it) and
+// E2 = rho0 <u Ab psi>_0 = A_x dWt, and the collision time from the two sides' pressures.
+template <class R>
+GKS_HD void interface_terms(const FluxParams<R>& P, R pl, R pr, const R q0[5], const Prim<R>& w0,
+                            const R dW[3][5], R dt, R dWt[5], R E0[5], R E1[5], R E2[5],
+                            R& tau) {
+  const R gm1 = P.gamma - R(1);
+  const R ir0 = w0.ir, Ep0 = q0[4] + w0.p;
+  R t[5];
+  euler_jvp(w0, ir0, gm1, Ep0, 0, dW[0], dWt);
+  euler_jvp(w0, ir0, gm1, Ep0, 1, dW[1], t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dWt[q] += t[q];
+  euler_jvp(w0, ir0, gm1, Ep0, 2, dW[2], t);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) dWt[q] = -(dWt[q] + t[q]);
+  euler_flux_x(w0, q0[4], E0);
+  euler_jvp(w0, ir0, gm1, Ep0, 0, dWt, E2);
+  const R dp = k_abs((pl - pr) / (pl + pr));
+  tau = collision_time(P, w0.p, ir0, dp, dt);
+  if (P.tau_model != 0) {
+    second_moment_jvp(w0, ir0, gm1, P.K, 0, dW[0], E1);
+#pragma unroll
+    for (int d = 1; d < 3; ++d) {
+      second_moment_jvp(w0, ir0, gm1, P.K, d, dW[d], t);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) E1[q] += t[q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) E1[q] = R(0);
+  }
+}
+
+// Smooth flux (Eq. flux-2) from the interface terms: F(delta) = E0 delta - tau delta (E1 + E2)
+// + delta^2/2 E2, so the two-point time fit is exact; with the heat-flux correction the energy
+// components gain pr_fix times the heat flux relative to the interface velocity, from the flux
+// moments F and the conserved moments m of the time-integrated distribution (m^n = Q0,
+// dm/dt = dWt; the tau terms of m vanish by the compatibility condition defining Ab).
+template <class R>
+GKS_HD void smooth_from_terms(const FluxParams<R>& P, const R q0[5], const Prim<R>& w0,
+                              const R dWt[5], const R E0[5], const R E1[5], const R E2[5], R tau,
+                              R Fn[5], R Ft[5]) {
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    Fn[q] = E0[q] - tau * (E1[q] + E2[q]);
+    Ft[q] = E2[q];
+  }
+  if (P.pr_fix != R(0)) {
+    const R u2 = w0.U * w0.U + w0.V * w0.V + w0.W * w0.W;
+    auto heat = [&](const R F[5], const R m[5]) {
+      return F[4] - (w0.U * F[1] + w0.V * F[2] + w0.W * F[3]) + R(0.5) * u2 * F[0] -
+             (w0.U * m[4] - w0.U * (w0.U * m[1] + w0.V * m[2] + w0.W * m[3]) +
+              R(0.5) * w0.U * u2 * m[0]);
+    };
+    const R qn = heat(Fn, q0);
+    const R qt = heat(Ft, dWt);
+    Fn[4] += P.pr_fix * qn;
+    Ft[4] += P.pr_fix * qt;
+  }
+}
+
 // Gauss-point flux in the local frame (u along the normal). ql/qr: conserved states;
 // dql/dqr[m]: their derivatives along n1, n2, n3 (momentum already in the local frame).
 // Writes Fn = F^n and Ft = dF/dt of the two-point time fit. Returns false for a non-physical
@@ -528,56 +594,10 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
 #pragma unroll
     for (int q = 0; q < 5; ++q) dW[d][q] += t[q];
   }
-  // equilibrium time slope, rho0 <Ab psi>_0 = -sum_d rho0 <c_d ab_d psi>_0 = -sum_d A_d dW_d,
-  // and the equilibrium flux moments E0 = rho0 <u psi>_0, E2 = rho0 <u Ab psi>_0 = A_x dWt
-  const R ir0 = w0.ir, Ep0 = q0[4] + w0.p;
-  R dWt[5], E0[5], E1[5], E2[5];
-  euler_jvp(w0, ir0, gm1, Ep0, 0, dW[0], dWt);
-  euler_jvp(w0, ir0, gm1, Ep0, 1, dW[1], t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) dWt[q] += t[q];
-  euler_jvp(w0, ir0, gm1, Ep0, 2, dW[2], t);
-#pragma unroll
-  for (int q = 0; q < 5; ++q) dWt[q] = -(dWt[q] + t[q]);
-  euler_flux_x(w0, q0[4], E0);
-  euler_jvp(w0, ir0, gm1, Ep0, 0, dWt, E2);
-  const R dp = k_abs((wl.p - wr.p) / (wl.p + wr.p));
-  const R tau = collision_time(P, w0.p, ir0, dp, dt);
-  if (P.tau_model != 0) {
-    // E1 = rho0 <u (ab . c) psi>_0 = sum_d D T_d(W0)[dW_d]
-    second_moment_jvp(w0, ir0, gm1, P.K, 0, dW[0], E1);
-#pragma unroll
-    for (int d = 1; d < 3; ++d) {
-      second_moment_jvp(w0, ir0, gm1, P.K, d, dW[d], t);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) E1[q] += t[q];
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 5; ++q) E1[q] = R(0);  // multiplied by tau = 0 in both flux forms
-  }
+  R dWt[5], E0[5], E1[5], E2[5], tau;
+  interface_terms(P, wl.p, wr.p, q0, w0, dW, dt, dWt, E0, E1, E2, tau);
   if (!P.full) {
-    // F(delta) = E0 delta - tau delta (E1 + E2) + delta^2/2 E2: the fit is exact.
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      Fn[q] = E0[q] - tau * (E1[q] + E2[q]);
-      Ft[q] = E2[q];
-    }
-    if (P.pr_fix != R(0)) {
-      // heat flux relative to the interface velocity, from the flux moments F and the conserved
-      // moments m of the time-integrated distribution: m^n = Q0, dm/dt = dWt (the tau terms of
-      // m vanish by the compatibility condition defining Ab)
-      const R u2 = w0.U * w0.U + w0.V * w0.V + w0.W * w0.W;
-      auto heat = [&](const R F[5], const R m[5]) {
-        return F[4] - (w0.U * F[1] + w0.V * F[2] + w0.W * F[3]) + R(0.5) * u2 * F[0] -
-               (w0.U * m[4] - w0.U * (w0.U * m[1] + w0.V * m[2] + w0.W * m[3]) +
-                R(0.5) * w0.U * u2 * m[0]);
-      };
-      const R qn = heat(Fn, q0);
-      const R qt = heat(Ft, dWt);
-      Fn[4] += P.pr_fix * qn;
-      Ft[4] += P.pr_fix * qt;
-    }
+    smooth_from_terms(P, q0, w0, dWt, E0, E1, E2, tau, Fn, Ft);
     return true;
   }
   // full flux: the non-equilibrium parts of both sides. With the side's slopes a_d (rho <a_d psi>
@@ -678,6 +698,39 @@ GKS_HD void eval_poly(const Coef& coef, const R d[3], R val[5], R grad[5][3]) {
   }
 }
 
+// The local frame of a Gauss point: n1 the unit normal, n2 = n1 x e_k / |n1 x e_k| with e_k the
+// axis least aligned with n1, n3 = n1 x n2.
+template <class R>
+GKS_HD void face_frame(const R n1[3], R n2[3], R n3[3]) {
+  int kk = 0;
+  if (k_abs(n1[1]) < k_abs(n1[kk])) kk = 1;
+  if (k_abs(n1[2]) < k_abs(n1[kk])) kk = 2;
+  if (kk == 0) { n2[0] = R(0); n2[1] = n1[2]; n2[2] = -n1[1]; }
+  else if (kk == 1) { n2[0] = -n1[2]; n2[1] = R(0); n2[2] = n1[0]; }
+  else { n2[0] = n1[1]; n2[1] = -n1[0]; n2[2] = R(0); }
+  const R il = R(1) / k_sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
+  n2[0] = n2[0] * il; n2[1] = n2[1] * il; n2[2] = n2[2] * il;
+  n3[0] = n1[1] * n2[2] - n1[2] * n2[1];
+  n3[1] = n1[2] * n2[0] - n1[0] * n2[2];
+  n3[2] = n1[0] * n2[1] - n1[1] * n2[0];
+}
+
+// A local-frame flux (F^n, dF/dt) rotated back to the global frame and weighted by the
+// quadrature weight w: acc[0..4] = w F^n, acc[5..9] = w dF/dt.
+template <class R>
+GKS_HD void rotate_flux_out(const R Fn[5], const R Ft[5], const R n1[3], const R n2[3],
+                            const R n3[3], R w, R acc[10]) {
+  acc[0] = w * Fn[0];
+  acc[4] = w * Fn[4];
+  acc[5] = w * Ft[0];
+  acc[9] = w * Ft[4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc[1 + a] = w * (Fn[1] * n1[a] + Fn[2] * n2[a] + Fn[3] * n3[a]);
+    acc[6 + a] = w * (Ft[1] * n1[a] + Ft[2] * n2[a] + Ft[3] * n3[a]);
+  }
+}
+
 // Whole Gauss-point contribution in the global frame. Left/right values and gradients are
 // rotated into the local frame (n1 the unit normal, n2 = n1 x e_k / |n1 x e_k| with e_k the axis
 // least aligned with n1, n3 = n1 x n2), the local flux is computed, rotated back and multiplied
@@ -685,17 +738,8 @@ GKS_HD void eval_poly(const Coef& coef, const R d[3], R val[5], R grad[5][3]) {
 template <class R>
 GKS_HD bool gp_flux_global(const FluxParams<R>& P, const R vl[5], const R gl[5][3], const R vr[5],
                            const R gr[5][3], const R n1[3], R w, R dt, R acc[10]) {
-  int kk = 0;
-  if (k_abs(n1[1]) < k_abs(n1[kk])) kk = 1;
-  if (k_abs(n1[2]) < k_abs(n1[kk])) kk = 2;
-  R n2[3];
-  if (kk == 0) { n2[0] = R(0); n2[1] = n1[2]; n2[2] = -n1[1]; }
-  else if (kk == 1) { n2[0] = -n1[2]; n2[1] = R(0); n2[2] = n1[0]; }
-  else { n2[0] = n1[1]; n2[1] = -n1[0]; n2[2] = R(0); }
-  const R il = R(1) / k_sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
-  n2[0] = n2[0] * il; n2[1] = n2[1] * il; n2[2] = n2[2] * il;
-  const R n3[3] = {n1[1] * n2[2] - n1[2] * n2[1], n1[2] * n2[0] - n1[0] * n2[2],
-                   n1[0] * n2[1] - n1[1] * n2[0]};
+  R n2[3], n3[3];
+  face_frame(n1, n2, n3);
   const R* nm[3] = {n1, n2, n3};
   R ql[5], qr[5], dql[3][5], dqr[3][5];
   ql[0] = vl[0]; ql[4] = vl[4]; qr[0] = vr[0]; qr[4] = vr[4];
@@ -721,15 +765,7 @@ GKS_HD bool gp_flux_global(const FluxParams<R>& P, const R vl[5], const R gl[5][
   }
   R Fn[5], Ft[5];
   if (!gks_gp_flux(P, ql, dql, qr, dqr, dt, Fn, Ft)) return false;
-  acc[0] = w * Fn[0];
-  acc[4] = w * Fn[4];
-  acc[5] = w * Ft[0];
-  acc[9] = w * Ft[4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    acc[1 + a] = w * (Fn[1] * n1[a] + Fn[2] * n2[a] + Fn[3] * n3[a]);
-    acc[6 + a] = w * (Ft[1] * n1[a] + Ft[2] * n2[a] + Ft[3] * n3[a]);
-  }
+  rotate_flux_out(Fn, Ft, n1, n2, n3, w, acc);
   return true;
 }
 
