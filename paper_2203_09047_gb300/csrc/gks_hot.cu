@@ -623,12 +623,17 @@ __device__ __forceinline__ void first_order_if_nonphysical(const R* __restrict__
 // the axis least aligned with n1, n3 = n1 x n2), computes F^n and dF/dt, rotates back and
 // weights by the quadrature weight; the four are summed with shuffles and written once.
 // kFull selects the flux form and kTau0 a zero collision time at compile time, so that each
-// instance carries only the arithmetic (and registers) of its own form. The FP32 smooth
-// instances do the two sides' work on packed f32x2 arithmetic (gp_flux_global_smooth2); they
-// hold more values per thread, and 6 resident blocks measured best (0.453 ms per launch on the
-// 64^3-cube mesh; 5 and 7 blocks 0.454 and 0.460, the scalar form at 7 blocks 0.477).
+// instance carries only the arithmetic (and registers) of its own form. The FP32 instances do
+// the two sides' work on packed f32x2 arithmetic (gp_flux_global2: the flux templates
+// instantiated with the pair type P2). Resident blocks per SM, measured: smooth form 6 (0.442 ms
+// per launch on the 64^3-cube mesh; 5 and 7 blocks 0.456 and 0.446; the scalar form at 7
+// blocks 0.477); full form 4 (6.53 ms per launch on the 128^3-cube explosion; 3 and 5 blocks
+// 6.99 and 7.44; the scalar form 7.06).
 #ifndef GKS_FLUX_SMOOTH_MIN_BLOCKS
 #define GKS_FLUX_SMOOTH_MIN_BLOCKS 6  // resident 128-thread blocks per SM, FP32 smooth flux
+#endif
+#ifndef GKS_FLUX_FULL_MIN_BLOCKS
+#define GKS_FLUX_FULL_MIN_BLOCKS 4  // resident 128-thread blocks per SM, FP32 full flux
 #endif
 #ifndef GKS_FLUX_FP64_MIN_BLOCKS
 #define GKS_FLUX_FP64_MIN_BLOCKS 1  // resident 128-thread blocks per SM, FP64 flux
@@ -661,7 +666,7 @@ struct FaceRec<double> {
 };
 
 template <class R, bool kFull, bool kTau0>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SMOOTH_MIN_BLOCKS)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? GKS_FLUX_FULL_MIN_BLOCKS : GKS_FLUX_SMOOTH_MIN_BLOCKS)
                                                       : GKS_FLUX_FP64_MIN_BLOCKS)
     k_flux(
     int64_t nf, int64_t nc, const int32_t* __restrict__ f_owner, const int32_t* __restrict__ f_nb,
@@ -699,8 +704,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? (kFull ? 4 : GKS_FLUX_SM
       wall_ghost(P, wall, wall_data(wall_tab, wall), vl, gl, vr, gr);  // the wall's ghost
     }
     bool ok;
-    if constexpr (sizeof(R) == 4 && !kFull)
-      ok = gp_flux_global_smooth2(P, vl, gl, vr, gr, n1, w, dt, acc);  // packed f32x2 sides
+    if constexpr (sizeof(R) == 4)
+      ok = gp_flux_global2(P, vl, gl, vr, gr, n1, w, dt, acc);  // both sides on packed f32x2
     else
       ok = gp_flux_global(P, vl, gl, vr, gr, n1, w, dt, acc);
     if (!ok) atomicOr(flag, kErrNonphysical);

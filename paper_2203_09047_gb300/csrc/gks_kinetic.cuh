@@ -112,15 +112,16 @@ GKS_HD void second_moment_jvp(const Prim<R>& w, R ir, R gm1, R K, int d, const R
   for (int k = 0; k < 5; ++k) out[k] = dq[0] * t[k] + w.rho * dt[k];
 }
 
-// Half-line equilibrium of one side (u > 0 for s = +1, u < 0 for s = -1) in closed form:
+// Half-line equilibrium of one side (u > 0 for s = +1, u < 0 for s = -1; s is an int, or a
+// packed pair of signs when R carries both sides) in closed form:
 // A = <1>, A1 = <u>, A2 = <u^2> over the half line, B = exp(-lam U^2) / (2 sqrt(pi lam)) and
 // S = <v^2 + w^2 + xi^2>, so that rho <psi> = rho (A, A1, V A, W A, (A2 + S A) / 2).
 template <class R>
 struct Half {
   R A, A1, A2, B, S;
 };
-template <class R>
-GKS_HD void half_init(const Prim<R>& w, R K, int s, Half<R>& h) {
+template <class R, class Sg>
+GKS_HD void half_init(const Prim<R>& w, R K, Sg s, Half<R>& h) {
   const R sl = k_sqrt(w.lam);
   h.A = R(0.5) * k_erfc(-R(s) * sl * w.U);
   h.B = R(0.28209479177387814) * k_exp(-w.lam * w.U * w.U) / sl;  // 1/(2 sqrt(pi))
@@ -142,8 +143,8 @@ GKS_HD void half_moments(const Prim<R>& w, const Half<R>& h, R Q[5]) {
 // dB = -B (2 lam U dU + (U^2 + 1/(2 lam)) dlam). Equals rho <a psi> (half line) for the slope a
 // of the Maxwellian with rho <a psi> = dq over the full line. No division: the reciprocals come
 // with the primitives.
-template <class R>
-GKS_HD void half_jvp(const Prim<R>& w, R gm1, R K, int s, const Half<R>& h, const R dq[5],
+template <class R, class Sg>
+GKS_HD void half_jvp(const Prim<R>& w, R gm1, R K, Sg s, const Half<R>& h, const R dq[5],
                      R dQ[5]) {
   const R ir = w.ir, hil = w.hil;
   const R dU = (dq[1] - w.U * dq[0]) * ir, dV = (dq[2] - w.V * dq[0]) * ir,
@@ -206,8 +207,8 @@ GKS_HD void dprim(const Prim<R>& w, R gm1, const R dq[5], DPrim<R>& d) {
   d.dlam = w.lam * dll;
   d.dhil = -w.hil * dll;
 }
-template <class R>
-GKS_HD void dhalf_line(const Prim<R>& w, int s, const HalfLine<R>& m, const DPrim<R>& d,
+template <class R, class Sg>
+GKS_HD void dhalf_line(const Prim<R>& w, Sg s, const HalfLine<R>& m, const DPrim<R>& d,
                        R dA[5]) {
   const R U = w.U, hil = w.hil;
   dA[0] = R(s) * m.B * (R(2) * w.lam * d.dU + U * d.dlam);
@@ -227,8 +228,8 @@ GKS_HD void half_flux(const Prim<R>& w, R K, const HalfLine<R>& m, R F[5]) {
   F[4] = R(0.5) * w.rho * (m.A[3] + S * m.A[1]);
 }
 // DF+[dq]
-template <class R>
-GKS_HD void half_flux_jvp(const Prim<R>& w, R gm1, R K, int s, const HalfLine<R>& m,
+template <class R, class Sg>
+GKS_HD void half_flux_jvp(const Prim<R>& w, R gm1, R K, Sg s, const HalfLine<R>& m,
                           const R dq[5], R out[5]) {
   DPrim<R> d;
   dprim(w, gm1, dq, d);
@@ -244,8 +245,8 @@ GKS_HD void half_flux_jvp(const Prim<R>& w, R gm1, R K, int s, const HalfLine<R>
                      w.rho * (dA[3] + dS * m.A[1] + S * dA[1]));
 }
 // DT+_k[dq] for the velocity component k (0 normal, 1, 2 tangential)
-template <class R>
-GKS_HD void half_second_jvp(const Prim<R>& w, R gm1, R K, int s, const HalfLine<R>& m, int k,
+template <class R, class Sg>
+GKS_HD void half_second_jvp(const Prim<R>& w, R gm1, R K, Sg s, const HalfLine<R>& m, int k,
                             const R dq[5], R out[5]) {
   DPrim<R> d;
   dprim(w, gm1, dq, d);
@@ -561,6 +562,29 @@ GKS_HD void smooth_from_terms(const FluxParams<R>& P, const R q0[5], const Prim<
   }
 }
 
+// Coefficients of the two-point time fit of the full flux: F^n and dF/dt are sums over the six
+// terms of Eq. flux-1 with weights cn and ct from the time integrals over [0, dt/2] and [0, dt]
+// (tau = 0: the equilibrium flux and its time derivative alone).
+template <class R>
+GKS_HD void full_fit_coeffs(R tau, R dt, R cn[6], R ct[6]) {
+  if (tau > R(0)) {
+    R ch[6], cf[6];
+    flux1_integrals(tau, R(0.5) * dt, ch);
+    flux1_integrals(tau, dt, cf);
+    const R idt = R(1) / dt;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      cn[q] = (R(4) * ch[q] - cf[q]) * idt;
+      ct[q] = R(4) * (cf[q] - R(2) * ch[q]) * idt * idt;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) cn[q] = ct[q] = R(0);
+    cn[0] = R(1);
+    ct[2] = R(1);
+  }
+}
+
 // Gauss-point flux in the local frame (u along the normal). ql/qr: conserved states;
 // dql/dqr[m]: their derivatives along n1, n2, n3 (momentum already in the local frame).
 // Writes Fn = F^n and Ft = dF/dt of the two-point time fit. Returns false for a non-physical
@@ -641,22 +665,7 @@ GKS_HD bool gks_gp_flux(const FluxParams<R>& P, const R ql[5],
     half_flux_jvp(wr, gm1, P.K, -1, mr, dtr, NR[2]);
   }
   R cn[6], ct[6];
-  if (tau > R(0)) {
-    R ch[6], cf[6];
-    flux1_integrals(tau, R(0.5) * dt, ch);
-    flux1_integrals(tau, dt, cf);
-    const R idt = R(1) / dt;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      cn[q] = (R(4) * ch[q] - cf[q]) * idt;
-      ct[q] = R(4) * (cf[q] - R(2) * ch[q]) * idt * idt;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) cn[q] = ct[q] = R(0);
-    cn[0] = R(1);
-    ct[2] = R(1);
-  }
+  full_fit_coeffs(tau, dt, cn, ct);
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     const R geq_n = cn[0] * E0[q] + cn[1] * E1[q] + cn[2] * E2[q];
