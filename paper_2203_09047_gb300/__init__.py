@@ -129,6 +129,8 @@ def load_library(path: str = LIB_PATH):
     L.gks_s2o4_stage_vjp.restype = st
     for name in ("gks_gp_flux_host", "gks_gp_flux_vjp_host", "gks_gp_face_host"):
         getattr(L, name).restype = ctypes.c_int
+    L.gks_gp_face_f32_pair.argtypes = [P, ctypes.c_int, P, P]
+    L.gks_gp_face_f32_pair.restype = ctypes.c_int
     L.gks_wall_ghost_host.argtypes = [P, ctypes.c_int] + [P] * 8
     L.gks_wall_ghost_host.restype = None
     L.gks_wall_flux_fix_host.argtypes = [P, ctypes.c_int, P]

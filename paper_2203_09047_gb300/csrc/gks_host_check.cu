@@ -1,8 +1,13 @@
 // Host instantiations of the Gauss-point flux and its vector-Jacobian product in FP64, running
 // the same templated arithmetic as the flux kernels. They let the kinetic formulas and their
-// hand-written adjoint be checked on a CPU (against the oracle and finite differences).
+// hand-written adjoint be checked on a CPU (against the oracle and finite differences). One
+// device entry runs the FP32 Gauss-point flux in its scalar and its packed f32x2 instantiation
+// side by side, a direct test of the pair arithmetic.
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
+#include "gks_flux_f32x2.cuh"
 #include "gks_kinetic_adj.cuh"
 
 namespace {
@@ -129,3 +134,60 @@ extern "C" void gks_wall_ghost_host(const double* p, int code, const double* v, 
 extern "C" void gks_wall_flux_fix_host(const double* p, int code, double* acc) {
   gks::wall_flux_fix(code, wall_from(p, code), acc);
 }
+
+namespace {
+gks::FluxParams<float> params_f32(const double* p) {
+  const gks::FluxParams<double> d = params_from(p);
+  gks::FluxParams<float> P;
+  P.gamma = (float)d.gamma;
+  P.K = (float)d.K;
+  P.mu = (float)d.mu;
+  P.tau_eps = (float)d.tau_eps;
+  P.tau_C = (float)d.tau_C;
+  P.full = d.full;
+  P.tau_model = d.tau_model;
+  P.pr_fix = (float)d.pr_fix;
+  P.T_ref = (float)d.T_ref;
+  P.mu_pow = (float)d.mu_pow;
+  return P;
+}
+// point i: in[45 i ..] = vl[5], gl[5][3], vr[5], gr[5][3], n1[3], w, dt;
+// out[21 i ..] = scalar acc[10], packed acc[10], (scalar ok) + 2 (packed ok)
+__global__ void k_face_f32_pair(gks::FluxParams<float> P, int n, const float* __restrict__ in,
+                                float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* x = in + 45 * (int64_t)i;
+  float vl[5], gl[5][3], vr[5], gr[5][3], n1[3];
+  for (int v = 0; v < 5; ++v) {
+    vl[v] = x[v];
+    vr[v] = x[20 + v];
+    for (int a = 0; a < 3; ++a) {
+      gl[v][a] = x[5 + 3 * v + a];
+      gr[v][a] = x[25 + 3 * v + a];
+    }
+  }
+  for (int a = 0; a < 3; ++a) n1[a] = x[40 + a];
+  const float w = x[43], dt = x[44];
+  float acc_s[10], acc_p[10];
+  const bool ok_s = gks::gp_flux_global(P, vl, gl, vr, gr, n1, w, dt, acc_s);
+  const bool ok_p = gks::gp_flux_global2(P, vl, gl, vr, gr, n1, w, dt, acc_p);
+  float* o = out + 21 * (int64_t)i;
+  for (int q = 0; q < 10; ++q) {
+    o[q] = acc_s[q];
+    o[10 + q] = acc_p[q];
+  }
+  o[20] = (ok_s ? 1.f : 0.f) + (ok_p ? 2.f : 0.f);
+}
+}  // namespace
+
+// The FP32 Gauss-point contribution on the GPU in the scalar and the packed f32x2
+// instantiation of the flux templates, for n points: in [n][45], out [n][21] (device
+// pointers, layout above), p the parameter vector of gks_gp_face_host. Synchronises the
+// device; 0 on success, 1 on a CUDA error.
+extern "C" int gks_gp_face_f32_pair(const double* p, int n, const float* in, float* out) {
+  if (n <= 0) return 0;
+  k_face_f32_pair<<<(n + 127) / 128, 128>>>(params_f32(p), n, in, out);
+  return cudaDeviceSynchronize() == cudaSuccess ? 0 : 1;
+}
+
