@@ -51,11 +51,13 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
                                                 const float gl[5][3], const float vr[5],
                                                 const float gr[5][3], const float n1[3],
                                                 float w, float dt, float acc[10]) {
-  float n2[3], n3[3];
-  face_frame(n1, n2, n3);
-  const float* const nm[3] = {n1, n2, n3};
   P2 q[5], dq[3][5];
-  rotate_in2(vl, gl, vr, gr, nm, q, dq);
+  {
+    float n2[3], n3[3];
+    face_frame(n1, n2, n3);
+    const float* const nm[3] = {n1, n2, n3};
+    rotate_in2(vl, gl, vr, gr, nm, q, dq);
+  }
   const P2 gm1(P.gamma - 1.f), K2(P.K), sg(1.f, -1.f);  // sg: u > 0 left, u < 0 right
   Prim<P2> ws;
   if (!to_prim(q, P2(P.gamma), ws)) return false;
@@ -69,8 +71,6 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
 #pragma unroll
     for (int v = 0; v < 5; ++v) q0[v] = hsum(Q[v]);
   }
-  Prim<float> w0;
-  if (!to_prim(q0, P.gamma, w0)) return false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     P2 t[5];
@@ -78,6 +78,8 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
 #pragma unroll
     for (int v = 0; v < 5; ++v) dW[d][v] = hsum(t[v]);
   }
+  Prim<float> w0;
+  if (!to_prim(q0, P.gamma, w0)) return false;
   float dWt[5], E0[5], E1[5], E2[5], tau, Fn[5], Ft[5];
   interface_terms(P, ws.p.lo(), ws.p.hi(), q0, w0, dW, dt, dWt, E0, E1, E2, tau);
   if (!P.full) {
@@ -115,6 +117,9 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
       Ft[v] = ct[0] * E0[v] + ct[1] * E1[v] + ct[2] * E2[v] + hsum(st);
     }
   }
+  // the frame again (cheaper than holding it through the flux)
+  float n2[3], n3[3];
+  face_frame(n1, n2, n3);
   rotate_flux_out(Fn, Ft, n1, n2, n3, w, acc);
   return true;
 }
