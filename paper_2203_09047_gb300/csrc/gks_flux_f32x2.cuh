@@ -52,9 +52,9 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
                                                 const float gr[5][3], const float n1[3],
                                                 float w, float dt, float acc[10]) {
   P2 q[5], dq[3][5];
+  float n2[3], n3[3];
+  face_frame(n1, n2, n3);
   {
-    float n2[3], n3[3];
-    face_frame(n1, n2, n3);
     const float* const nm[3] = {n1, n2, n3};
     rotate_in2(vl, gl, vr, gr, nm, q, dq);
   }
@@ -71,6 +71,12 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
 #pragma unroll
     for (int v = 0; v < 5; ++v) q0[v] = hsum(Q[v]);
   }
+  // the smooth form holds fewer values through the slopes with the interface primitives
+  // formed after them and the frame formed again at the end (measured: 0.438 against 0.442 ms
+  // per launch on the 64^3-cube mesh); the full form runs faster as written first (6.53
+  // against 6.61 ms on the 128^3-cube explosion)
+  Prim<float> w0;
+  if (P.full && !to_prim(q0, P.gamma, w0)) return false;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     P2 t[5];
@@ -78,8 +84,7 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
 #pragma unroll
     for (int v = 0; v < 5; ++v) dW[d][v] = hsum(t[v]);
   }
-  Prim<float> w0;
-  if (!to_prim(q0, P.gamma, w0)) return false;
+  if (!P.full && !to_prim(q0, P.gamma, w0)) return false;
   float dWt[5], E0[5], E1[5], E2[5], tau, Fn[5], Ft[5];
   interface_terms(P, ws.p.lo(), ws.p.hi(), q0, w0, dW, dt, dWt, E0, E1, E2, tau);
   if (!P.full) {
@@ -117,9 +122,7 @@ __device__ __forceinline__ bool gp_flux_global2(const FluxParams<float>& P, cons
       Ft[v] = ct[0] * E0[v] + ct[1] * E1[v] + ct[2] * E2[v] + hsum(st);
     }
   }
-  // the frame again (cheaper than holding it through the flux)
-  float n2[3], n3[3];
-  face_frame(n1, n2, n3);
+  if (!P.full) face_frame(n1, n2, n3);
   rotate_flux_out(Fn, Ft, n1, n2, n3, w, acc);
   return true;
 }
