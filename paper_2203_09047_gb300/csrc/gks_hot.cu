@@ -280,6 +280,20 @@ struct PolyPair<double> {
   }
 };
 
+// Quotients of the weights and the output scaling: the FP32 path uses the fast division
+// intrinsic (x times an approximate reciprocal, within 2 ulp for divisors below 2^126: the
+// indicators, weights and cell sizes here), the FP64 path the IEEE division. Against IEEE
+// divisions in FP32: 0.436 -> 0.417 ms per pass on the 64^3-cube mesh (the weights of phase 3
+// take about a dozen quotients per thread).
+template <class R>
+__device__ __forceinline__ R wdiv(R a, R b) {
+  return a / b;
+}
+template <>
+__device__ __forceinline__ float wdiv<float>(float a, float b) {
+  return __fdividef(a, b);
+}
+
 // Five resident blocks per SM as the register bound (at most 80 registers a thread; 72 used):
 // on the 64^3-cube hybrid mesh with the enlarged stencils 0.598 ms per FP32 pass, 0.611 ms at 6
 // blocks (64 registers, spills); before the rows went through L2, 0.664 ms against 0.697 ms
@@ -492,9 +506,9 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
                     a[8] * a[8];
     R tau = R(0);
     for (int s = 0; s < M; ++s) tau += fabs(beta0 - sbet[(5 * s + v) * kTile + lane]);
-    tau /= R(M);
+    tau = wdiv(tau, R(M));
     auto weight = [&](R gam, R bb) {
-      const R r = tau / (bb + weps);
+      const R r = wdiv(tau, bb + weps);
       R pw = r;
       for (int q = 1; q < wpow; ++q) pw *= r;
       return gam * (R(1) + pw);
@@ -507,9 +521,10 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
       wm[s] = s < M ? weight(wg, sbet[(5 * s + v) * kTile + lane]) : R(0);
       sum += wm[s];
     }
-    const R is = R(1) / sum;
+    const R is = wdiv(R(1), sum);
     const R wb0 = w0 * is;
-    const R corr = wb0 * wg / g0;
+    const R ig0 = wdiv(R(1), g0);
+    const R corr = wb0 * wg * ig0;
     // phase 4 (same warp, same variable): linear part of the combination and the output
     R cl[3] = {R(0), R(0), R(0)};
 #pragma unroll
@@ -520,7 +535,7 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
         for (int t = 0; t < 3; ++t) cl[t] += f * sb[((3 * s + t) * 5 + v) * kTile + lane];
       }
     }
-    const R ca = wb0 / g0;
+    const R ca = wb0 * ig0;
     R C[9];
 #pragma unroll
     for (int n = 0; n < 9; ++n) C[n] = ca * a[n];
@@ -528,7 +543,7 @@ __global__ void __launch_bounds__(kReconThreads, kReconBlocksPerSM) k_recon(
     C[1] += cl[1];
     C[2] += cl[2];
     {
-      const R ih = R(1) / hc, ih2 = ih * ih;
+      const R ih = wdiv(R(1), hc), ih2 = ih * ih;
       // Q = c0 + c1 dx + c2 dy + c3 dz + c4 dx^2 + c5 dy^2 + c6 dz^2 + c7 dxdy + c8 dxdz + c9 dydz
       const R shift = C[3] * m2[0] + C[4] * m2[1] + C[5] * m2[2] + C[6] * m2[3] +
                       C[7] * m2[4] + C[8] * m2[5];
