@@ -70,6 +70,9 @@ __device__ __forceinline__ bool operator!=(const P2& a, const P2& b) {
   return (a.v.x != b.v.x) || (a.v.y != b.v.y);
 }
 
+__device__ __forceinline__ P2 k_div(const P2& a, const P2& b) {
+  return P2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
+}
 __device__ __forceinline__ P2 k_sqrt(const P2& x) { return P2(sqrtf(x.v.x), sqrtf(x.v.y)); }
 __device__ __forceinline__ P2 k_exp(const P2& x) { return P2(expf(x.v.x), expf(x.v.y)); }
 __device__ __forceinline__ P2 k_erfc(const P2& x) { return P2(erfcf(x.v.x), erfcf(x.v.y)); }

@@ -23,6 +23,22 @@ GKS_HD double k_abs(double x) { return fabs(x); }
 GKS_HD float k_abs(float x) { return fabsf(x); }
 GKS_HD double k_pow(double x, double y) { return pow(x, y); }
 GKS_HD float k_pow(float x, float y) { return powf(x, y); }
+// Quotients of the per-state terms (reciprocals of rho and p, the half-line B, the frame
+// normalisation, the pressure jump): the IEEE division, except for FP32 on the device, which
+// takes the fast division intrinsic (within 2 ulp for divisors below 2^126). FP32 flux per
+// launch, against IEEE divisions: smooth form 0.438 -> 0.421 ms on the 64^3-cube mesh, full
+// form 6.52 -> 6.12 ms on the 128^3-cube explosion.
+template <class R>
+GKS_HD R k_div(R a, R b) {
+  return a / b;
+}
+GKS_HD float k_div(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
 
 template <class R>
 struct Prim {
@@ -34,12 +50,12 @@ struct Prim {
 template <class R>
 GKS_HD bool to_prim(const R q[5], R gamma, Prim<R>& w) {
   w.rho = q[0];
-  w.ir = R(1) / q[0];
+  w.ir = k_div(R(1), q[0]);
   w.U = q[1] * w.ir;
   w.V = q[2] * w.ir;
   w.W = q[3] * w.ir;
   w.p = (gamma - R(1)) * (q[4] - R(0.5) * (q[1] * w.U + q[2] * w.V + q[3] * w.W));
-  w.ip = R(1) / w.p;
+  w.ip = k_div(R(1), w.p);
   w.lam = R(0.5) * w.rho * w.ip;
   w.hil = w.p * w.ir;
   return (w.rho > R(0)) && (w.p > R(0));  // false also for NaN
@@ -124,7 +140,7 @@ template <class R, class Sg>
 GKS_HD void half_init(const Prim<R>& w, R K, Sg s, Half<R>& h) {
   const R sl = k_sqrt(w.lam);
   h.A = R(0.5) * k_erfc(-R(s) * sl * w.U);
-  h.B = R(0.28209479177387814) * k_exp(-w.lam * w.U * w.U) / sl;  // 1/(2 sqrt(pi))
+  h.B = k_div(R(0.28209479177387814) * k_exp(-w.lam * w.U * w.U), sl);  // 1/(2 sqrt(pi))
   h.A1 = w.U * h.A + R(s) * h.B;
   h.A2 = w.U * h.A1 + w.hil * h.A;
   h.S = w.V * w.V + w.W * w.W + (K + R(2)) * w.hil;
@@ -518,7 +534,7 @@ GKS_HD void interface_terms(const FluxParams<R>& P, R pl, R pr, const R q0[5], c
   for (int q = 0; q < 5; ++q) dWt[q] = -(dWt[q] + t[q]);
   euler_flux_x(w0, q0[4], E0);
   euler_jvp(w0, ir0, gm1, Ep0, 0, dWt, E2);
-  const R dp = k_abs((pl - pr) / (pl + pr));
+  const R dp = k_abs(k_div(pl - pr, pl + pr));
   tau = collision_time(P, w0.p, ir0, dp, dt);
   if (P.tau_model != 0) {
     second_moment_jvp(w0, ir0, gm1, P.K, 0, dW[0], E1);
@@ -717,7 +733,7 @@ GKS_HD void face_frame(const R n1[3], R n2[3], R n3[3]) {
   if (kk == 0) { n2[0] = R(0); n2[1] = n1[2]; n2[2] = -n1[1]; }
   else if (kk == 1) { n2[0] = -n1[2]; n2[1] = R(0); n2[2] = n1[0]; }
   else { n2[0] = n1[1]; n2[1] = -n1[0]; n2[2] = R(0); }
-  const R il = R(1) / k_sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]);
+  const R il = k_div(R(1), k_sqrt(n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2]));
   n2[0] = n2[0] * il; n2[1] = n2[1] * il; n2[2] = n2[2] * il;
   n3[0] = n1[1] * n2[2] - n1[2] * n2[1];
   n3[1] = n1[2] * n2[0] - n1[0] * n2[2];
