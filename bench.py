@@ -492,7 +492,7 @@ def run_gpu(args):
     # smooth flux from the ncu captures on the 48^3-cube mesh with the enlarged stencils
     # (profiles/k_recon_float_advection48_ncu.md, profiles/k_flux_float_smooth_advection48_ncu.md),
     # scaled by cells and by faces (same layer pattern and stencils)
-    dram_per_unit = {"recon": (1550.3, nc), "flux": (292.0, nf)}
+    dram_per_unit = {"recon": (1552.3, nc), "flux": (292.0, nf)}
 
     def roof_of(table, dom, is_mixed):
         if dom == "flux":
